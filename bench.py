@@ -1,0 +1,439 @@
+"""Benchmark of the GB300 grid-hashing KNN hot path.
+
+One step is the whole hot path over one batch: index build (box, Eq. 1 keys,
+sort by cell, cell offsets, cell table, row gather) followed by the batched
+query (layer walk, top-k, vote or mean) of every query of the workload.
+Inputs are resident in HBM when the timed region starts; L2 is flushed before
+every timed step.  Throughput is queries per second of whole steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config NAME]
+  python bench.py --impl reference ...   # the CPU oracle on this host's cores
+
+Under torchrun (N > 1) every rank runs its own replica of the workload (the
+queries of the method are independent problems; no data crosses ranks) and
+the result is the total over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2004_02290_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "queries/sec (index build + batched query per step)"
+UNIT = "queries/s"
+L2_FLUSH_BYTES = 512 << 20
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "query_kernel_large_cls_ncu.md")
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--config", default="large_cls", choices=list(wl.SPECS))
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-sample", type=int, default=50_000,
+                   help="queries of the oracle's bounded sample")
+    return p.parse_args(argv)
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def aggregate(units_local: float, seconds_local: float, world: int):
+    """Whole-job throughput: units of all ranks over the slowest rank's time."""
+    if world <= 1:
+        return units_local / seconds_local, seconds_local
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([seconds_local], dtype=torch.float64, device=dev)
+    u = torch.tensor([units_local], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()) / float(t.item()), float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (the reference arm and the cpu_baseline leg)
+# ---------------------------------------------------------------------------
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_step(w: wl.Workload, sample: int, offset: int = 0):
+    """Time the oracle on the full build and a bounded sample of queries.
+
+    Returns (scaled seconds for the whole workload, details)."""
+    import oracle
+
+    cores = host_cores()
+    t0 = time.perf_counter()
+    g = oracle.Grid(w.points, w.labels, w.w)
+    t_build = time.perf_counter() - t0
+    s = min(sample, w.m)
+    start = (offset * s) % w.m
+    idx = (np.arange(s) + start) % w.m
+    q = np.ascontiguousarray(w.queries[idx])
+    chunks = np.array_split(np.arange(s), cores * 4)
+    t1 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:  # ctypes releases the GIL
+        list(ex.map(lambda c: g.query(q[c], w.k, w.mode) if len(c) else None, chunks))
+    t_query = time.perf_counter() - t1
+    g.close()
+    scaled = t_build + t_query * (w.m / s)
+    return scaled, {"build_s": t_build, "query_s": t_query, "sample_queries": s, "cores": cores}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = wl.make(args.config)
+    times = []
+    det = None
+    for i in range(args.warmup + args.steps):
+        sec, det = oracle_step(w, min(args.cpu_sample, 20_000), offset=i)
+        if i >= args.warmup:
+            times.append(sec)
+    mean = float(np.mean(times))
+    value = w.m / mean
+    sample = (f"full build of n={w.n} + {det['sample_queries']} of {w.m} queries per step "
+              f"({det['cores']} threads), scaled to the workload")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": mean * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(w, "n/a (CPU)"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": det["cores"], "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def workload_config(w: wl.Workload, l2: str):
+    return {"workload": w.name, "n": w.n, "d": w.d, "m": w.m, "k": w.k,
+            "mode": "vote" if w.mode == wl.VOTE else "mean", "cell_width": w.w,
+            "table": {0: "auto", 1: "dense", 2: "hash"}[w.table], "l2": l2}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, power = [], [], []
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "power_w_max": float(max(power)) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# roofline accounting
+# ---------------------------------------------------------------------------
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def query_kernel_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("query_kernel.cuh", "ghn_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2004_02290_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per launch of the query kernel from the committed ncu summary,
+    if it was taken on the current kernel source and this workload."""
+    if not os.path.exists(PROFILE_SUMMARY):
+        return None
+    with open(PROFILE_SUMMARY) as f:
+        text = f.read()
+    sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    wk = re.search(r"workload:\s*(\S+)", text)
+    tr = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not (sha and wk and tr) or sha.group(1) != query_kernel_sha() or wk.group(1) != workload:
+        return None
+    return float(tr.group(1))
+
+
+def method_bytes(w: wl.Workload, stats: np.ndarray, row_floats: int, table: int) -> float:
+    """Algorithmic bytes of one query launch: per query, the query row, one
+    table entry per occupied cell of the visited layers, one stored row per
+    point examined, the k ids and distances, the prediction and the k winners'
+    outputs (counters from the exhaustive walk, equal to the oracle's)."""
+    entry = 16 if table == 2 else 8
+    cells = float(stats[:, 1].sum())
+    cands = float(stats[:, 2].sum())
+    per_query_fixed = 4 * w.d + 8 * w.k + 4 + 4 * w.k
+    return w.m * per_query_fixed + entry * cells + 4 * row_floats * cands
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+
+    from paper_2004_02290_gb300 import knn
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    knn.library()
+
+    w = wl.make(args.config)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        pts = torch.from_numpy(w.points).to(dev)
+        lab = torch.from_numpy(w.labels).to(dev)
+        q = torch.from_numpy(w.queries).to(dev)
+        ids = torch.empty((w.m, w.k), dtype=torch.int32, device=dev)
+        d2 = torch.empty((w.m, w.k), dtype=torch.float32, device=dev)
+        pred = torch.empty(w.m, dtype=torch.int32 if w.mode == wl.VOTE else torch.float32,
+                           device=dev)
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize(dev)
+    flags = knn.KNN_QUERY_SORTED
+
+    def step(phases):
+        idx = knn.knn_build(pts, lab, w.w, w.table, stream=stream)
+        if phases is not None:
+            phases.extend(("build." + n, t) for n, t in knn.knn_timing_read())
+        knn.knn_query(idx, q, w.k, w.mode, flags=flags, stream=stream, ids=ids, dist2=d2,
+                      pred=pred)
+        if phases is not None:
+            phases.extend(("query." + n, t) for n, t in knn.knn_timing_read())
+        idx.free()
+
+    knn.knn_timing_enable(True)
+    for _ in range(args.warmup):
+        flush.zero_()
+        step([])
+    torch.cuda.synchronize(dev)
+
+    # the timed region
+    sampler = ClockSampler(local)
+    sampler.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    launches0 = knn.knn_kernel_launches()
+    step_ms, phase_tot = [], {}
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()  # evict the inputs from L2 before each step
+            ev0.record(stream)
+        phases = []
+        step(phases)
+        with torch.cuda.stream(stream):
+            ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        for n, t in phases:
+            phase_tot[n] = phase_tot.get(n, 0.0) + t
+    torch.cuda.synchronize(dev)
+    launches = knn.knn_kernel_launches() - launches0
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    knn.knn_timing_enable(False)
+
+    total_s = sum(step_ms) / 1e3
+    value, max_s = aggregate(float(w.m * args.steps), total_s, world)
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel ----
+    phase_ms = {n: t / args.steps for n, t in phase_tot.items()}
+    dominant = max(phase_ms, key=phase_ms.get)
+    idx = knn.knn_build(pts, lab, w.w, w.table, stream=stream)
+    info = idx.info()
+    _, _, st = knn.knn_query_stats(idx, q, w.k, stream=stream)
+    stats = st.cpu().numpy()
+    idx.free()
+    peaks, peak_kind = measured_peaks()
+    q_ms = phase_ms["query.search"]
+    mbytes = method_bytes(w, stats, info.row_floats, info.table)
+    traffic = profiled_traffic(w.name)
+    roof = {
+        "kernel": "query_kernel (query.search)",
+        "dominant_phase": dominant,
+        "bound": "hbm",
+        "achieved": mbytes / (q_ms * 1e-3) / 1e9,
+        "peak": float(peaks["hbm_gbs"]),
+        "peak_kind": f"{peak_kind} (HBM copy, MEASURED_PEAKS.json hbm_gbs)",
+        "unit": "GB/s",
+        "traffic": traffic,
+        "algorithmic_bytes_per_launch": mbytes,
+        "launch_ms": q_ms,
+    }
+    roof["frac"] = roof["achieved"] / roof["peak"]
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(w, knn, dev, args)
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        sec, det = oracle_step(w, args.cpu_sample)
+        cpu = {"value": w.m / sec, "unit": UNIT, "cores": det["cores"], "kind": "oracle",
+               "sample": (f"full oracle build of n={w.n} ({det['build_s']:.2f} s) + "
+                          f"{det['sample_queries']} of {w.m} queries on {det['cores']} threads "
+                          f"({det['query_s']:.2f} s), query time scaled to all {w.m}")}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": max_s * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": workload_config(w, "flushed before every step (512 MiB write)"),
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "gpu_launches": int(launches),
+        "phase_ms": {k: round(v, 4) for k, v in sorted(phase_ms.items())},
+        "build_points_per_s": w.n / ((sum(v for k, v in phase_ms.items()
+                                          if k.startswith("build."))) * 1e-3),
+        "query_only_per_s": w.m / (sum(v for k, v in phase_ms.items()
+                                       if k.startswith("query.")) * 1e-3),
+        "layers_mean": float(stats[:, 0].mean()),
+        "step_ms_median": float(np.median(step_ms)),
+    }
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_e2e(w, knn, dev, args):
+    """Same step through the C ABI with pinned host buffers: the library copies
+    the inputs in and the results out inside the timed region."""
+    import torch
+
+    pts = torch.from_numpy(w.points).pin_memory()
+    lab = torch.from_numpy(w.labels).pin_memory()
+    q = torch.from_numpy(w.queries).pin_memory()
+    ids = torch.empty((w.m, w.k), dtype=torch.int32).pin_memory()
+    d2 = torch.empty((w.m, w.k), dtype=torch.float32).pin_memory()
+    pred = torch.empty(w.m, dtype=torch.int32 if w.mode == wl.VOTE else torch.float32).pin_memory()
+    h2d = pts.numel() * 4 + lab.numel() * 4 + q.numel() * 4
+    d2h = ids.numel() * 4 + d2.numel() * 4 + pred.numel() * 4
+
+    def step():
+        idx = knn.knn_build(pts, lab, w.w, w.table)
+        knn.knn_query(idx, q, w.k, w.mode, flags=knn.KNN_QUERY_SORTED, ids=ids, dist2=d2,
+                      pred=pred)
+        idx.free()
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize(dev)
+    n = max(3, min(args.steps, 20))
+    t0 = time.perf_counter()
+    for _ in range(n):
+        step()
+    torch.cuda.synchronize(dev)
+    sec = (time.perf_counter() - t0) / n
+    return {"value": w.m / sec, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": sec * 1e3}
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

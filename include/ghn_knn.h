@@ -1,0 +1,181 @@
+/*
+ * ghn_knn.h: C ABI of the GB300 grid-hashing nearest-neighbour library.
+ *
+ * The method is GHN ("Grid Hashing Neighborhood", Tchaye-Kondi, Zhai, Zhu,
+ * arXiv 2004.02290).  Training points are hashed to the cells of a virtual
+ * grid (Sec. III.A, Eq. 1, Algorithm 1).  A query starts from its own cell and
+ * visits the surrounding cells layer by layer, keeping the k nearest points
+ * seen so far, until a layer brings no update (Sec. III.B, Algorithm 2).  The
+ * neighbours' outputs then give a majority vote (classification) or a mean
+ * (regression) (Sec. I, Sec. III.D).
+ *
+ * Conventions shared by every entry point:
+ *   - Pointers are plain host or device pointers.  Arguments documented as
+ *     "host or device" may point to either; the library asks the CUDA driver
+ *     which one it is and stages host data through device memory itself.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Device work is ordered on it.
+ *   - Inputs are borrowed: the library copies what it keeps before the call's
+ *     work on `stream` completes.  Outputs are owned by the caller.
+ *   - Every function returns a knn_status; on failure knn_last_error() holds
+ *     a message for the calling thread.
+ *   - One device per index: the device current at knn_build time.
+ *
+ * Readings of points the paper leaves open, fixed by this library:
+ *   - origin: per-dimension minimum of the training points; one cell width
+ *     for all dimensions, given by the caller.
+ *   - cell id (Eq. 1): c_j = floor((p_j - o_j) / w) in IEEE single precision,
+ *     round to nearest; cells are half-open; query cells are clamped to
+ *     [-2^40, 2^40].
+ *   - layer L: the cells at Chebyshev distance L from the central cell.
+ *   - stop: after layer L when the k-buffer is full and no point of layer L
+ *     entered it, or when the layers so far cover every occupied cell.
+ *   - order: (squared distance, training index) ascending; squared distance
+ *     in single precision, dimension order, no fused multiply-add.
+ *   - fewer than k points found: ids padded with -1, distances with +inf.
+ *   - vote: largest count, ties to the smallest label.  mean: double-precision
+ *     sum in neighbour order divided by the count, rounded to single.
+ */
+#ifndef GHN_KNN_H
+#define GHN_KNN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define KNN_OK 0
+#define KNN_EINVAL 1 /* bad argument or input outside what the index can hold */
+#define KNN_ENOMEM 2 /* device or host allocation failed */
+#define KNN_ECUDA 3  /* a CUDA call failed; knn_last_error() has its text */
+#define KNN_ELIMIT 4 /* a query reached the layer cap; its rows are -1 / +inf */
+typedef int32_t knn_status;
+
+/* Prediction modes (Sec. I: majority class, or average of the outputs). */
+#define KNN_NONE -1 /* neighbours only; pred is ignored and may be NULL */
+#define KNN_VOTE 0  /* labels are int32 classes; pred receives int32 */
+#define KNN_MEAN 1  /* labels are float targets; pred receives float */
+
+/* Cell tables (Sec. III.A: a hash table keyed by the cell id, no empty cells). */
+#define KNN_TABLE_AUTO 0  /* dense when the cell box has at most 4n + 1024 cells */
+#define KNN_TABLE_DENSE 1 /* direct table over the bounding box of occupied cells */
+#define KNN_TABLE_HASH 2  /* open addressing over occupied cells only */
+
+/* knn_query flags. */
+#define KNN_QUERY_CHECKED 1 /* synchronize `stream` and return the kernel's status */
+#define KNN_QUERY_SORTED 2  /* visit queries in cell order (locality in L2) */
+
+typedef struct ghn_index ghn_index; /* opaque; owns all of its device memory */
+
+/* Shape of a built index, for inspection (knn_index_info). */
+typedef struct {
+    int64_t n;           /* training points */
+    int32_t d;           /* dimensions */
+    int32_t table;       /* KNN_TABLE_DENSE or KNN_TABLE_HASH */
+    float cell_width;    /* w */
+    float origin[8];     /* per-dimension minimum of the training points */
+    int64_t extent[8];   /* cells per dimension in the box of occupied cells */
+    int64_t num_cells;   /* occupied cells (at most n) */
+    int64_t table_slots; /* dense entries or hash slots in use */
+    int32_t row_floats;  /* floats per stored point row (2, 4 or 8) */
+    int32_t has_labels;  /* 1 when labels were given */
+} knn_index_info_t;
+
+/*
+ * knn_build: cell sampling (Sec. III.A, Eq. 1, Algorithm 1).
+ *   points      host or device, n*d float32, row-major (point i at points[i*d]).
+ *   labels      host or device, n 32-bit outputs (int32 classes or float
+ *               targets, kept as raw bits), or NULL (neighbours only).
+ *   n           1 <= n < 2^31.
+ *   d           1 <= d <= 8.
+ *   cell_width  w > 0, finite.
+ *   table       KNN_TABLE_AUTO / _DENSE / _HASH.
+ *   stream      cudaStream_t or NULL.
+ *   out         receives the new index; NULL on failure.
+ * Errors: KNN_EINVAL for a bad argument, a non-finite coordinate, more than
+ * 2^31 - 1 cells along one dimension, more than 2^63 cells in the box, or a
+ * dense table of more than 2^31 entries; KNN_ENOMEM; KNN_ECUDA.
+ * The call synchronizes `stream` once, to read the box of occupied cells.
+ */
+knn_status knn_build(const float* points, const void* labels, int64_t n, int32_t d,
+                     float cell_width, int32_t table, void* stream, ghn_index** out);
+
+/*
+ * knn_query: exploration and prediction (Sec. III.B, Algorithm 2; Sec. I).
+ *   index    from knn_build.
+ *   queries  host or device, m*d float32, row-major.
+ *   m        m >= 0 (0 is a no-op).
+ *   k        1 <= k <= 64.
+ *   mode     KNN_NONE / KNN_VOTE / KNN_MEAN (VOTE and MEAN need labels).
+ *   ids      host or device, m*k int32: training indices, nearest first.
+ *   dist2    host or device, m*k float32 squared distances (may be NULL).
+ *   pred     host or device, m int32 (VOTE) or float32 (MEAN), or NULL.
+ *   flags    KNN_QUERY_CHECKED | KNN_QUERY_SORTED.
+ *   stream   cudaStream_t or NULL.
+ * Device outputs are written asynchronously on `stream`; host outputs are
+ * filled before the call returns.  A query with a non-finite coordinate gets
+ * -1 / +inf rows (KNN_EINVAL under KNN_QUERY_CHECKED); a query that reaches
+ * the layer cap set by the GHN_MAX_LAYERS environment variable (0 or unset:
+ * no cap) gets -1 / +inf rows (KNN_ELIMIT under KNN_QUERY_CHECKED).
+ */
+knn_status knn_query(const ghn_index* index, const float* queries, int64_t m, int32_t k,
+                     int32_t mode, int32_t* ids, float* dist2, void* pred, int32_t flags,
+                     void* stream);
+
+/*
+ * knn_query_stats: the same walk with every cell of every visited layer
+ * looked up (no geometric skipping), reporting per query the work the method
+ * defines (Sec. III.C: exploration depth and points processed).
+ *   ids, dist2  as knn_query (device or host; dist2 may be NULL).
+ *   stats       host or device, m*3 int64: {layers visited (L* + 1),
+ *               occupied cells looked up, training points examined}.
+ * Synchronizes `stream` and returns the kernel's status.
+ */
+knn_status knn_query_stats(const ghn_index* index, const float* queries, int64_t m, int32_t k,
+                           int32_t* ids, float* dist2, int64_t* stats, void* stream);
+
+/* Shape of the index.  Synchronizes the index's build stream on first use. */
+knn_status knn_index_info(const ghn_index* index, knn_index_info_t* info);
+
+/*
+ * knn_index_export: the grid as built, for inspection and tests.
+ *   cell_keys   host, num_cells uint64: linear cell ids, ascending; the id of
+ *               cell c is sum_j c_j * prod_{i>j} extent_i.
+ *   cell_start  host, num_cells + 1 uint32: first stored row of each cell.
+ *   rows        host, n int32: training index of each stored row (cell order,
+ *               ascending index inside a cell).
+ * Any pointer may be NULL.  Synchronizes the device.
+ */
+knn_status knn_index_export(const ghn_index* index, uint64_t* cell_keys, uint32_t* cell_start,
+                            int32_t* rows);
+
+/*
+ * Phase timing, for profiling.  While enabled, knn_build and knn_query record
+ * a CUDA event on the call's stream at each phase boundary (build: stage, box,
+ * keys, sort, cells, table, gather; query: stage, order, search, copy).
+ * knn_timing_read waits for the last call's events on the calling thread and
+ * writes up to `cap` phase names (static strings) and device milliseconds;
+ * it returns the number of phases.
+ */
+knn_status knn_timing_enable(int32_t on);
+int32_t knn_timing_read(const char** names, float* ms, int32_t cap);
+
+/* Kernels this library has launched in this process (all threads). */
+int64_t knn_kernel_launches(void);
+
+/* Release the index (NULL is a no-op).  Waits for work that uses it. */
+void knn_free(ghn_index* index);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* knn_last_error(void);
+
+/* ABI version: 1. */
+int32_t knn_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GHN_KNN_H */

@@ -1,0 +1,667 @@
+// Index build kernels: cell sampling (Sec. III.A, Eq. 1, Algorithm 1) on the GPU.
+//
+// Algorithm 1 appends every training point to the list of its cell in a
+// dictionary keyed by the cell id.  Here the same grouping is a stable sort of
+// the points by a linear cell id, followed by run-length cell offsets, a cell
+// table (dense over the box of occupied cells, or open addressing over the
+// occupied cells only: "no information about empty cells", Sec. III.A) and a
+// gather of the point rows into cell order.  Stable sorting keeps the points
+// of a cell in ascending training index, which is Algorithm 1's append order.
+//
+// Every kernel is a streaming pass bound by HBM bandwidth; none is a dense
+// contraction, so tensor cores have no role here.
+
+#include "ghn_internal.cuh"
+
+#include <math.h>
+
+namespace ghn {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// ---------------------------------------------------------------------------
+// Box of the training points: per-dimension min / max and a finiteness check.
+// A block has 64*d threads and the grid stride is a multiple of d, so every
+// thread always sees the same dimension (threadIdx.x % d) of the row-major
+// array, and the loads of a warp are contiguous.
+// ---------------------------------------------------------------------------
+__global__ void box_partial_kernel(const float* __restrict__ pts, long long total, int d,
+                                   float* __restrict__ partial)
+{
+    extern __shared__ float sm[];
+    float* slo = sm;
+    float* shi = sm + blockDim.x;
+    __shared__ int sbad;
+    const int t = threadIdx.x;
+    if (t == 0) sbad = 0;
+    float lo = INFINITY, hi = -INFINITY;
+    bool bad = false;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long e = (long long)blockIdx.x * blockDim.x + t; e < total; e += stride) {
+        const float v = __ldg(pts + e);
+        bad |= !isfinite(v);
+        lo = fminf(lo, v);
+        hi = fmaxf(hi, v);
+    }
+    slo[t] = lo;
+    shi[t] = hi;
+    __syncthreads();
+    if (bad) sbad = 1;
+    if (t < d) {
+        for (int u = t + d; u < (int)blockDim.x; u += d) {
+            lo = fminf(lo, slo[u]);
+            hi = fmaxf(hi, shi[u]);
+        }
+    }
+    __syncthreads();
+    float* out = partial + (size_t)blockIdx.x * (2 * d + 1);
+    if (t < d) {
+        out[t] = lo;
+        out[d + t] = hi;
+    }
+    if (t == 0) out[2 * d] = sbad ? 1.0f : 0.0f;
+}
+
+// Reduce the partial boxes; compute the number of cells per dimension from the
+// largest point: ext_j = floor((hi_j - lo_j) / w) + 1 (Eq. 1 is monotone in
+// the coordinate, so no training point has a larger cell coordinate).
+__global__ void box_final_kernel(const float* __restrict__ partial, int nblocks, int d, float w,
+                                 BoxOut* __restrict__ out)
+{
+    const int j = threadIdx.x;
+    __shared__ unsigned int flags;
+    if (j == 0) flags = 0u;
+    __syncthreads();
+    if (j < d) {
+        float lo = INFINITY, hi = -INFINITY;
+        bool bad = false;
+        for (int b = 0; b < nblocks; ++b) {
+            const float* p = partial + (size_t)b * (2 * d + 1);
+            lo = fminf(lo, p[j]);
+            hi = fmaxf(hi, p[d + j]);
+            bad |= p[2 * d] != 0.0f;
+        }
+        out->lo[j] = lo;
+        out->hi[j] = hi;
+        long long ext = 0;
+        if (bad || !(lo <= hi)) {
+            atomicOr(&flags, kStatusNonFinite);
+        } else {
+            const float t = __fdiv_rn(__fsub_rn(hi, lo), w);
+            if (!(t < 2147483647.0f)) {
+                atomicOr(&flags, kStatusExtent);
+            } else {
+                ext = (long long)floorf(t) + 1;
+            }
+        }
+        out->ext[j] = ext;
+    }
+    __syncthreads();
+    if (j == 0) out->flags = flags;
+}
+
+// ---------------------------------------------------------------------------
+// Eq. 1 for every training point: c_j = floor((p_j - o_j) / w) in single
+// precision (subtract and divide rounded to nearest, as IEEE operations), then
+// the linear id sum_j c_j * stride_j; the value is the point's index.
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void cell_keys_kernel(const float* __restrict__ pts, long long n, GridConst g,
+                                 unsigned long long* __restrict__ keys,
+                                 unsigned int* __restrict__ vals)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        unsigned long long key = 0;
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            const float t = __fdiv_rn(__fsub_rn(__ldg(pts + i * D + j), g.lo[j]), g.w);
+            const long long c = (long long)floorf(t);
+            key += (unsigned long long)c * g.stride[j];
+        }
+        keys[i] = key;
+        vals[i] = (unsigned int)i;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Stable LSD radix sort, 8-bit digits, 2048-element tiles (256 threads x 8).
+// Per pass: a digit histogram per tile, an exclusive scan of the digit-major
+// histogram table, and a scatter that ranks each tile stably in shared memory
+// and writes it out in digit runs.
+// ---------------------------------------------------------------------------
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kRadix = 256;
+
+__global__ void __launch_bounds__(kSortThreads)
+    radix_hist_kernel(const unsigned long long* __restrict__ keys, long long n, int shift,
+                      unsigned int* __restrict__ hist, unsigned int nb)
+{
+    __shared__ unsigned int cnt[kRadix];
+    const int t = threadIdx.x;
+    cnt[t] = 0u;
+    __syncthreads();
+    const long long base = (long long)blockIdx.x * kSortTile;
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const long long i = base + r * kSortThreads + t;
+        const bool valid = i < n;
+        const unsigned dg = valid ? (unsigned)((keys[i] >> shift) & 0xffu) : 0x100u + (t & 31);
+        const unsigned peers = __match_any_sync(FULL, dg);
+        if (valid && (peers & lanemask_lt()) == 0u) atomicAdd(&cnt[dg], __popc(peers));
+    }
+    __syncthreads();
+    hist[(size_t)t * nb + blockIdx.x] = cnt[t];
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+    radix_scatter_kernel(const unsigned long long* __restrict__ kin,
+                         const unsigned int* __restrict__ vin,
+                         unsigned long long* __restrict__ kout, unsigned int* __restrict__ vout,
+                         long long n, int shift, const unsigned int* __restrict__ scanned,
+                         unsigned int nb)
+{
+    constexpr int W = kSortThreads / 32;
+    __shared__ unsigned int wcnt[W][kRadix];
+    __shared__ unsigned int dig_off[kRadix];
+    __shared__ unsigned int gbase[kRadix];
+    __shared__ unsigned int wsum[W];
+    __shared__ unsigned long long skey[kSortTile];
+    __shared__ unsigned int sval[kSortTile];
+
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    for (int e = t; e < W * kRadix; e += kSortThreads) (&wcnt[0][0])[e] = 0u;
+    gbase[t] = scanned[(size_t)t * nb + blockIdx.x];
+    __syncthreads();
+
+    const long long tile = (long long)blockIdx.x * kSortTile;
+    const long long count = n - tile < kSortTile ? n - tile : kSortTile;
+    unsigned long long k[kSortItems];
+    unsigned int v[kSortItems], rank[kSortItems], dg[kSortItems];
+    // warp `warp` ranks elements [warp*256, warp*256+256) of the tile, in order
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const int local = warp * (32 * kSortItems) + r * 32 + lane;
+        const bool valid = local < count;
+        k[r] = valid ? kin[tile + local] : 0ull;
+        v[r] = valid ? vin[tile + local] : 0u;
+        const unsigned d = valid ? (unsigned)((k[r] >> shift) & 0xffu) : 0x100u + lane;
+        const unsigned peers = __match_any_sync(FULL, d);
+        const unsigned before = __popc(peers & lanemask_lt());
+        unsigned int b = 0u;
+        if (valid) b = wcnt[warp][d];
+        __syncwarp();
+        if (valid && before == 0u) wcnt[warp][d] = b + __popc(peers);
+        __syncwarp();
+        rank[r] = b + before;
+        dg[r] = d;
+    }
+    __syncthreads();
+    // per digit: exclusive prefix over warps, and the tile's total
+    unsigned int run = 0u;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        const unsigned int c = wcnt[w][t];
+        wcnt[w][t] = run;
+        run += c;
+    }
+    // exclusive scan of the 256 digit totals (one per thread)
+    unsigned int x = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    unsigned int wpre = 0u;
+    for (int w = 0; w < warp; ++w) wpre += wsum[w];
+    dig_off[t] = wpre + x - run;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        if (dg[r] < 0x100u) {
+            const unsigned int p = dig_off[dg[r]] + wcnt[warp][dg[r]] + rank[r];
+            skey[p] = k[r];
+            sval[p] = v[r];
+        }
+    }
+    __syncthreads();
+    for (int i = t; i < count; i += kSortThreads) {
+        const unsigned long long key = skey[i];
+        const unsigned d = (unsigned)((key >> shift) & 0xffu);
+        const unsigned int g = gbase[d] + (unsigned int)i - dig_off[d];
+        kout[g] = key;
+        vout[g] = sval[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive prefix sum of uint32: reduce per 1024-element block, scan the
+// block sums in one block, then scan each block and add its offset.
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 4;
+constexpr int kScanBlock = kScanThreads * kScanItems;
+
+// Inclusive block scan of one value per thread; returns the inclusive value
+// and writes the block total to *total.
+__device__ __forceinline__ unsigned int block_scan_incl(unsigned int x, unsigned int* wsum,
+                                                        unsigned int* total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned int s = lane < nw ? wsum[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int y = __shfl_up_sync(FULL, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < nw) wsum[lane] = s;
+    }
+    __syncthreads();
+    const unsigned int pre = warp > 0 ? wsum[warp - 1] : 0u;
+    *total = wsum[nw - 1];
+    __syncthreads();
+    return x + pre;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+    scan_reduce_kernel(const unsigned int* __restrict__ in, long long n,
+                       unsigned int* __restrict__ sums)
+{
+    __shared__ unsigned int wsum[32];
+    const long long base = (long long)blockIdx.x * kScanBlock + threadIdx.x * kScanItems;
+    unsigned int s = 0u;
+#pragma unroll
+    for (int r = 0; r < kScanItems; ++r)
+        if (base + r < n) s += in[base + r];
+    unsigned int total;
+    block_scan_incl(s, wsum, &total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) scan_spine_kernel(unsigned int* __restrict__ sums,
+                                                          long long nb)
+{
+    __shared__ unsigned int wsum[32];
+    unsigned int carry = 0u;
+    for (long long base = 0; base < nb; base += blockDim.x) {
+        const long long i = base + threadIdx.x;
+        const unsigned int x = i < nb ? sums[i] : 0u;
+        unsigned int total;
+        const unsigned int incl = block_scan_incl(x, wsum, &total);
+        if (i < nb) sums[i] = carry + incl - x;
+        carry += total;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+    scan_down_kernel(const unsigned int* in, unsigned int* out, long long n,
+                     const unsigned int* __restrict__ sums)
+{
+    __shared__ unsigned int wsum[32];
+    const long long base = (long long)blockIdx.x * kScanBlock + threadIdx.x * kScanItems;
+    unsigned int v[kScanItems];
+    unsigned int s = 0u;
+#pragma unroll
+    for (int r = 0; r < kScanItems; ++r) {
+        v[r] = base + r < n ? in[base + r] : 0u;
+        s += v[r];
+    }
+    unsigned int total;
+    unsigned int run = block_scan_incl(s, wsum, &total) - s + sums[blockIdx.x];
+#pragma unroll
+    for (int r = 0; r < kScanItems; ++r) {
+        if (base + r < n) out[base + r] = run;
+        run += v[r];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Cells: a head flag where the sorted id changes; the exclusive scan of the
+// flags numbers the cells.  Each head writes its cell's id and first row.
+// ---------------------------------------------------------------------------
+__global__ void head_flags_kernel(const unsigned long long* __restrict__ keys, long long n,
+                                  unsigned int* __restrict__ flags)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        flags[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
+}
+
+__global__ void cells_write_kernel(const unsigned long long* __restrict__ keys, long long n,
+                                   const unsigned int* __restrict__ flags,
+                                   const unsigned int* __restrict__ cid,
+                                   unsigned long long* __restrict__ cell_key,
+                                   unsigned int* __restrict__ cell_start, GridDev* gdev)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        if (flags[i]) {
+            cell_key[cid[i]] = keys[i];
+            cell_start[cid[i]] = (unsigned int)i;
+        }
+        if (i == n - 1) {
+            const unsigned long long u = cid[i] + flags[i];
+            cell_start[u] = (unsigned int)n;
+            unsigned long long cap = 16ull;
+            while (cap < 2ull * u) cap <<= 1;
+            gdev->ncells = u;
+            gdev->hmask = cap - 1ull;
+        }
+    }
+}
+
+// Dense table: the row count of every occupied cell at its linear id, zeros
+// elsewhere; an exclusive scan of that array gives each cell's first row.
+__global__ void dense_counts_kernel(const unsigned long long* __restrict__ cell_key,
+                                    const unsigned int* __restrict__ cell_start,
+                                    const GridDev* __restrict__ gdev,
+                                    unsigned int* __restrict__ dstart)
+{
+    const unsigned long long u = gdev->ncells;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < (long long)u;
+         c += stride)
+        dstart[cell_key[c]] = cell_start[c + 1] - cell_start[c];
+}
+
+// Open addressing with linear probing over a power-of-two table at most half
+// full, so every insert finds an empty slot.
+__global__ void hash_clear_kernel(HashSlot* __restrict__ slots, const GridDev* __restrict__ gdev)
+{
+    const unsigned long long cap = gdev->hmask + 1ull;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < (long long)cap;
+         s += stride) {
+        HashSlot e;
+        e.key = kEmptyKey;
+        e.start = 0u;
+        e.end = 0u;
+        slots[s] = e;
+    }
+}
+
+__global__ void hash_insert_kernel(const unsigned long long* __restrict__ cell_key,
+                                   const unsigned int* __restrict__ cell_start,
+                                   const GridDev* __restrict__ gdev, HashSlot* slots)
+{
+    const unsigned long long u = gdev->ncells, mask = gdev->hmask;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < (long long)u;
+         c += stride) {
+        const unsigned long long key = cell_key[c];
+        unsigned long long h = mix64(key) & mask;
+        for (unsigned long long probe = 0; probe <= mask; ++probe) {
+            const unsigned long long prev = atomicCAS(&slots[h].key, kEmptyKey, key);
+            if (prev == kEmptyKey) {
+                slots[h].start = cell_start[c];
+                slots[h].end = cell_start[c + 1];
+                break;
+            }
+            h = (h + 1ull) & mask;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Gather the point rows into cell order, padded to 2, 4 or 8 floats so that a
+// row is one 8-, 16- or two 16-byte loads in the query kernel.
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void gather_kernel(const float* __restrict__ pts, long long n,
+                              const unsigned int* __restrict__ order, float* __restrict__ rows)
+{
+    constexpr int P = row_floats(D);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+        const long long i = order[r];
+        float v[P];
+#pragma unroll
+        for (int j = 0; j < P; ++j) v[j] = j < D ? __ldg(pts + i * D + j) : 0.0f;
+        if constexpr (P == 2) {
+            reinterpret_cast<float2*>(rows)[r] = make_float2(v[0], v[1]);
+        } else {
+#pragma unroll
+            for (int h = 0; h < P / 4; ++h)
+                reinterpret_cast<float4*>(rows)[r * (P / 4) + h] =
+                    make_float4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
+        }
+    }
+}
+
+// Cell id of each query clamped into the box (for the locality order only).
+template <int D>
+__global__ void query_keys_kernel(const float* __restrict__ q, long long m, GridConst g,
+                                  unsigned long long* __restrict__ keys,
+                                  unsigned int* __restrict__ vals)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        unsigned long long key = 0;
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            float t = floorf(__fdiv_rn(__fsub_rn(__ldg(q + i * D + j), g.lo[j]), g.w));
+            t = fminf(fmaxf(t, 0.0f), (float)g.cmax[j]);  // NaN becomes 0
+            long long c = (long long)t;
+            if (c > g.cmax[j]) c = g.cmax[j];
+            key += (unsigned long long)c * g.stride[j];
+        }
+        keys[i] = key;
+        vals[i] = (unsigned int)i;
+    }
+}
+
+int grid_for(long long work, int threads)
+{
+    long long b = (work + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 152 * 32) b = 152 * 32;
+    return (int)b;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+
+int box_partial_blocks(long long n)
+{
+    long long b = (n + 255) / 256;
+    if (b < 1) b = 1;
+    if (b > 152 * 4) b = 152 * 4;
+    return (int)b;
+}
+
+cudaError_t launch_box(const float* pts, long long n, int d, float w, float* partial,
+                       int partial_blocks, BoxOut* out, cudaStream_t s)
+{
+    const int threads = 64 * d;
+    box_partial_kernel<<<partial_blocks, threads, 2 * threads * sizeof(float), s>>>(
+        pts, n * d, d, partial);
+    box_final_kernel<<<1, 32, 0, s>>>(partial, partial_blocks, d, w, out);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cell_keys(const float* pts, long long n, const GridConst& g,
+                             unsigned long long* keys, unsigned int* vals, cudaStream_t s)
+{
+    const int b = grid_for(n, 256);
+    count_launches(1);
+    switch (g.d) {
+    case 1: cell_keys_kernel<1><<<b, 256, 0, s>>>(pts, n, g, keys, vals); break;
+    case 2: cell_keys_kernel<2><<<b, 256, 0, s>>>(pts, n, g, keys, vals); break;
+    case 3: cell_keys_kernel<3><<<b, 256, 0, s>>>(pts, n, g, keys, vals); break;
+    case 4: cell_keys_kernel<4><<<b, 256, 0, s>>>(pts, n, g, keys, vals); break;
+    case 5: cell_keys_kernel<5><<<b, 256, 0, s>>>(pts, n, g, keys, vals); break;
+    case 6: cell_keys_kernel<6><<<b, 256, 0, s>>>(pts, n, g, keys, vals); break;
+    case 7: cell_keys_kernel<7><<<b, 256, 0, s>>>(pts, n, g, keys, vals); break;
+    case 8: cell_keys_kernel<8><<<b, 256, 0, s>>>(pts, n, g, keys, vals); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_query_keys(const float* q, long long m, const GridConst& g,
+                              unsigned long long* keys, unsigned int* vals, cudaStream_t s)
+{
+    const int b = grid_for(m, 256);
+    count_launches(1);
+    switch (g.d) {
+    case 1: query_keys_kernel<1><<<b, 256, 0, s>>>(q, m, g, keys, vals); break;
+    case 2: query_keys_kernel<2><<<b, 256, 0, s>>>(q, m, g, keys, vals); break;
+    case 3: query_keys_kernel<3><<<b, 256, 0, s>>>(q, m, g, keys, vals); break;
+    case 4: query_keys_kernel<4><<<b, 256, 0, s>>>(q, m, g, keys, vals); break;
+    case 5: query_keys_kernel<5><<<b, 256, 0, s>>>(q, m, g, keys, vals); break;
+    case 6: query_keys_kernel<6><<<b, 256, 0, s>>>(q, m, g, keys, vals); break;
+    case 7: query_keys_kernel<7><<<b, 256, 0, s>>>(q, m, g, keys, vals); break;
+    case 8: query_keys_kernel<8><<<b, 256, 0, s>>>(q, m, g, keys, vals); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+size_t scan_temp_bytes(long long n)
+{
+    const long long nb = (n + kScanBlock - 1) / kScanBlock;
+    return (size_t)(nb > 0 ? nb : 1) * sizeof(unsigned int);
+}
+
+cudaError_t scan_exclusive(const unsigned int* in, unsigned int* out, long long n, void* temp,
+                           cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const long long nb = (n + kScanBlock - 1) / kScanBlock;
+    unsigned int* sums = static_cast<unsigned int*>(temp);
+    scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, sums);
+    scan_spine_kernel<<<1, 1024, 0, s>>>(sums, nb);
+    scan_down_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, sums);
+    count_launches(3);
+    return cudaGetLastError();
+}
+
+size_t radix_temp_bytes(long long n)
+{
+    const long long nb = (n + kSortTile - 1) / kSortTile;
+    const long long entries = (nb > 0 ? nb : 1) * kRadix;
+    size_t hist = (size_t)entries * sizeof(unsigned int);
+    hist = (hist + 255) & ~(size_t)255;
+    return hist + scan_temp_bytes(entries);
+}
+
+cudaError_t radix_sort_pairs(unsigned long long* keys_a, unsigned int* vals_a,
+                             unsigned long long* keys_b, unsigned int* vals_b, long long n,
+                             int bits, void* temp, unsigned long long** result_keys,
+                             unsigned int** result_vals, cudaStream_t s)
+{
+    const long long nb = (n + kSortTile - 1) / kSortTile;
+    const long long entries = nb * kRadix;
+    unsigned int* hist = static_cast<unsigned int*>(temp);
+    size_t hist_bytes = ((size_t)entries * sizeof(unsigned int) + 255) & ~(size_t)255;
+    void* scan_tmp = static_cast<char*>(temp) + hist_bytes;
+    unsigned long long *kin = keys_a, *kout = keys_b;
+    unsigned int *vin = vals_a, *vout = vals_b;
+    for (int shift = 0; shift < bits && n > 1; shift += 8) {
+        radix_hist_kernel<<<(unsigned)nb, kSortThreads, 0, s>>>(kin, n, shift, hist,
+                                                                 (unsigned)nb);
+        cudaError_t e = scan_exclusive(hist, hist, entries, scan_tmp, s);
+        if (e != cudaSuccess) return e;
+        radix_scatter_kernel<<<(unsigned)nb, kSortThreads, 0, s>>>(kin, vin, kout, vout, n, shift,
+                                                                    hist, (unsigned)nb);
+        count_launches(2);
+        unsigned long long* tk = kin;
+        kin = kout;
+        kout = tk;
+        unsigned int* tv = vin;
+        vin = vout;
+        vout = tv;
+    }
+    *result_keys = kin;
+    *result_vals = vin;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cells(const unsigned long long* sorted_keys, long long n,
+                         unsigned int* flags_tmp, unsigned int* cid_tmp, void* scan_tmp,
+                         unsigned long long* cell_key, unsigned int* cell_start, GridDev* gdev,
+                         cudaStream_t s)
+{
+    const int b = grid_for(n, 256);
+    head_flags_kernel<<<b, 256, 0, s>>>(sorted_keys, n, flags_tmp);
+    cudaError_t e = scan_exclusive(flags_tmp, cid_tmp, n, scan_tmp, s);
+    if (e != cudaSuccess) return e;
+    cells_write_kernel<<<b, 256, 0, s>>>(sorted_keys, n, flags_tmp, cid_tmp, cell_key, cell_start,
+                                         gdev);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dense_table(const unsigned long long* cell_key, const unsigned int* cell_start,
+                               const GridDev* gdev, unsigned long long ncell_space,
+                               unsigned int* dstart, void* scan_tmp, cudaStream_t s)
+{
+    // dstart has ncell_space + 1 entries; the last one ends up as n.
+    cudaError_t e = cudaMemsetAsync(dstart, 0, (ncell_space + 1) * sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    dense_counts_kernel<<<grid_for((long long)ncell_space, 256), 256, 0, s>>>(cell_key, cell_start,
+                                                                             gdev, dstart);
+    count_launches(1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return scan_exclusive(dstart, dstart, (long long)ncell_space + 1, scan_tmp, s);
+}
+
+cudaError_t launch_hash_table(const unsigned long long* cell_key, const unsigned int* cell_start,
+                              const GridDev* gdev, HashSlot* slots, unsigned long long max_slots,
+                              cudaStream_t s)
+{
+    hash_clear_kernel<<<grid_for((long long)max_slots, 256), 256, 0, s>>>(slots, gdev);
+    hash_insert_kernel<<<grid_for((long long)(max_slots / 2), 256), 256, 0, s>>>(cell_key,
+                                                                                cell_start, gdev,
+                                                                                slots);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const float* pts, long long n, int d, const unsigned int* order,
+                          float* rows, cudaStream_t s)
+{
+    const int b = grid_for(n, 256);
+    count_launches(1);
+    switch (d) {
+    case 1: gather_kernel<1><<<b, 256, 0, s>>>(pts, n, order, rows); break;
+    case 2: gather_kernel<2><<<b, 256, 0, s>>>(pts, n, order, rows); break;
+    case 3: gather_kernel<3><<<b, 256, 0, s>>>(pts, n, order, rows); break;
+    case 4: gather_kernel<4><<<b, 256, 0, s>>>(pts, n, order, rows); break;
+    case 5: gather_kernel<5><<<b, 256, 0, s>>>(pts, n, order, rows); break;
+    case 6: gather_kernel<6><<<b, 256, 0, s>>>(pts, n, order, rows); break;
+    case 7: gather_kernel<7><<<b, 256, 0, s>>>(pts, n, order, rows); break;
+    case 8: gather_kernel<8><<<b, 256, 0, s>>>(pts, n, order, rows); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace ghn

@@ -1,0 +1,844 @@
+// C ABI of the GB300 grid-hashing KNN library: argument checks, device memory,
+// host staging and the order of the build and query kernels on the caller's
+// stream.  The entry points are declared, with their contracts, in
+// include/ghn_knn.h.
+
+#include "ghn_internal.cuh"
+#include "../../include/ghn_knn.h"
+
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <atomic>
+#include <mutex>
+
+using namespace ghn;
+
+struct ghn_index {
+    int device = 0;
+    long long n = 0;
+    int d = 0;
+    float w = 0.0f;
+    int table = KNN_TABLE_DENSE;
+    GridConst g{};
+    unsigned long long ncell_space = 0;  // cells in the box (prod of extents)
+    int key_bits = 0;
+    float* rows = nullptr;           // n * row_floats(d), cell order
+    unsigned int* rid = nullptr;     // n training indices, cell order
+    unsigned int* labels = nullptr;  // n outputs, training order (or null)
+    unsigned int* dstart = nullptr;  // dense table
+    HashSlot* slots = nullptr;       // hash table
+    unsigned long long max_slots = 0;
+    GridDev* gdev = nullptr;
+    cudaEvent_t last_use = nullptr;
+    // filled on first inspection
+    bool info_ready = false;
+    GridDev host_gdev{};
+};
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+void set_err(const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+knn_status cuda_fail(cudaError_t e, const char* what)
+{
+    set_err("%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? KNN_ENOMEM : KNN_ECUDA;
+}
+
+#define GHN_CHECK(call, what)                          \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+// ---- allocation (stream-ordered pool), with a host-side failure injector ----
+
+std::atomic<long long> g_alloc_count{0};
+
+long long fail_alloc_at()
+{
+    static long long v = [] {
+        const char* s = getenv("GHN_FAIL_ALLOC_AT");
+        return s ? atoll(s) : 0ll;
+    }();
+    return v;
+}
+
+long long max_layers_env()
+{
+    static long long v = [] {
+        const char* s = getenv("GHN_MAX_LAYERS");
+        return s ? atoll(s) : 0ll;
+    }();
+    return v;
+}
+
+// ---- phase timing (knn_timing_enable / knn_timing_read) ----
+
+std::atomic<int> g_timing_on{0};
+std::atomic<long long> g_launches{0};
+
+struct PhaseTimer {
+    static constexpr int kMax = 16;
+    cudaEvent_t ev[kMax + 1] = {};
+    const char* names[kMax] = {};
+    int count = 0;     // phases recorded by the last call
+    int device = -1;
+    bool active = false;
+
+    void begin(cudaStream_t s)
+    {
+        active = g_timing_on.load() != 0;
+        count = 0;
+        if (!active) return;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (device != dev) {
+            for (auto& e : ev)
+                if (e) cudaEventDestroy(e);
+            for (auto& e : ev) cudaEventCreate(&e);
+            device = dev;
+        }
+        cudaEventRecord(ev[0], s);
+    }
+    void mark(const char* name, cudaStream_t s)
+    {
+        if (!active || count >= kMax) return;
+        names[count] = name;
+        cudaEventRecord(ev[count + 1], s);
+        ++count;
+    }
+};
+
+thread_local PhaseTimer g_timer;
+
+std::once_flag g_pool_once[64];
+
+void tune_pool(int dev)
+{
+    if (dev < 0 || dev >= 64) return;
+    std::call_once(g_pool_once[dev], [dev] {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            unsigned long long keep = ~0ull;  // keep freed blocks for reuse
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+    });
+}
+
+template <class T>
+knn_status dalloc(T** p, size_t count, cudaStream_t s, const char* what)
+{
+    *p = nullptr;
+    const long long nth = ++g_alloc_count;
+    const long long at = fail_alloc_at();
+    if (at > 0 && nth == at) {
+        set_err("%s: allocation %lld failed (injected by GHN_FAIL_ALLOC_AT)", what, nth);
+        return KNN_ENOMEM;
+    }
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(p), bytes, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        set_err("%s: cudaMallocAsync of %zu bytes failed: %s", what, bytes, cudaGetErrorString(e));
+        return KNN_ENOMEM;
+    }
+    return KNN_OK;
+}
+
+template <class T>
+void dfree(T*& p, cudaStream_t s)
+{
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+}
+
+// Frees every registered temporary on scope exit.
+struct Temps {
+    cudaStream_t s;
+    void* ptrs[24];
+    int n = 0;
+    explicit Temps(cudaStream_t s_) : s(s_) {}
+    template <class T>
+    knn_status alloc(T** p, size_t count, const char* what)
+    {
+        knn_status st = dalloc(p, count, s, what);
+        if (st == KNN_OK) ptrs[n++] = *p;
+        return st;
+    }
+    ~Temps()
+    {
+        for (int i = 0; i < n; ++i) cudaFreeAsync(ptrs[i], s);
+    }
+};
+
+bool is_device_ptr(const void* p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Device view of a caller buffer: the pointer itself when it is device memory,
+// else a temporary (copied in when `in` is set).
+template <class T>
+knn_status device_view(const T* user, size_t count, bool in, Temps& tmp, T** out,
+                       const char* what)
+{
+    if (!user) {
+        *out = nullptr;
+        return KNN_OK;
+    }
+    if (is_device_ptr(user)) {
+        *out = const_cast<T*>(user);
+        return KNN_OK;
+    }
+    knn_status st = tmp.alloc(out, count, what);
+    if (st != KNN_OK) return st;
+    if (in) GHN_CHECK(cudaMemcpyAsync(*out, user, count * sizeof(T), cudaMemcpyHostToDevice, tmp.s),
+                      what);
+    return KNN_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int num_sms(int dev)
+{
+    static int cache[64] = {0};
+    if (dev >= 0 && dev < 64 && cache[dev]) return cache[dev];
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    if (v <= 0) v = 1;
+    if (dev >= 0 && dev < 64) cache[dev] = v;
+    return v;
+}
+
+void free_index(ghn_index* x)
+{
+    if (!x) return;
+    DeviceGuard dg(x->device);
+    cudaStream_t s = 0;
+    if (x->last_use) cudaStreamWaitEvent(s, x->last_use, 0);
+    dfree(x->rows, s);
+    dfree(x->rid, s);
+    dfree(x->labels, s);
+    dfree(x->dstart, s);
+    dfree(x->slots, s);
+    dfree(x->gdev, s);
+    if (x->last_use) cudaEventDestroy(x->last_use);
+    delete x;
+}
+
+knn_status build_impl(const float* points_user, const void* labels_user, long long n, int d,
+                      float w, int table, cudaStream_t s, ghn_index** out)
+{
+    int dev = 0;
+    GHN_CHECK(cudaGetDevice(&dev), "cudaGetDevice");
+    tune_pool(dev);
+    ghn_index* x = new ghn_index();
+    // on failure: wait for the work already queued on the stream, then release
+    auto fail = [&](knn_status code) {
+        cudaStreamSynchronize(s);
+        cudaGetLastError();
+        free_index(x);
+        return code;
+    };
+    x->device = dev;
+    x->n = n;
+    x->d = d;
+    x->w = w;
+    knn_status st = KNN_OK;
+    g_timer.begin(s);
+    {
+        Temps tmp(s);
+        const float* pts = nullptr;
+        float* pts_dev = nullptr;
+        st = device_view(points_user, (size_t)(n * d), true, tmp, &pts_dev, "points");
+        pts = pts_dev;
+        const unsigned int* lab_in = nullptr;
+        if (st == KNN_OK && labels_user) {
+            unsigned int* lv = nullptr;
+            st = device_view(static_cast<const unsigned int*>(labels_user), (size_t)n, true, tmp,
+                             &lv, "labels");
+            lab_in = lv;
+        }
+        g_timer.mark("stage", s);
+        // ---- box of the training points and cells per dimension (one sync) ----
+        const int pb = box_partial_blocks(n);
+        float* partial = nullptr;
+        BoxOut* box_dev = nullptr;
+        if (st == KNN_OK) st = tmp.alloc(&partial, (size_t)pb * (2 * d + 1), "box partials");
+        if (st == KNN_OK) st = tmp.alloc(&box_dev, 1, "box");
+        if (st != KNN_OK) {
+            return fail(st);
+        }
+        BoxOut box;
+        cudaError_t e = launch_box(pts, n, d, w, partial, pb, box_dev, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&box, box_dev, sizeof(box), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            return fail(cuda_fail(e, "box"));
+        }
+        g_timer.mark("box", s);
+        if (box.flags & kStatusNonFinite) {
+            set_err("knn_build: a training coordinate is not finite");
+            return fail(KNN_EINVAL);
+        }
+        if (box.flags & kStatusExtent) {
+            set_err("knn_build: more than 2^31 - 1 cells along one dimension (cell width too small)");
+            return fail(KNN_EINVAL);
+        }
+        GridConst& g = x->g;
+        memset(&g, 0, sizeof(g));
+        g.w = w;
+        g.d = d;
+        unsigned long long space = 1ull;
+        bool overflow = false;
+        for (int j = 0; j < d; ++j) {
+            g.lo[j] = box.lo[j];
+            g.cmax[j] = box.ext[j] - 1;
+            const unsigned long long ext = (unsigned long long)box.ext[j];
+            if (space > (0x7fffffffffffffffull / ext)) overflow = true;
+            space *= ext;
+        }
+        if (overflow) {
+            set_err("knn_build: more than 2^63 cells in the box of the points (cell width too small)");
+            return fail(KNN_EINVAL);
+        }
+        unsigned long long stride = 1ull;
+        for (int j = d - 1; j >= 0; --j) {
+            g.stride[j] = stride;
+            stride *= (unsigned long long)box.ext[j];
+        }
+        x->ncell_space = space;
+        int bits = 0;
+        while (bits < 64 && (1ull << bits) < space) ++bits;
+        x->key_bits = bits;
+        if (table == KNN_TABLE_AUTO)
+            table = space <= 4ull * (unsigned long long)n + 1024ull ? KNN_TABLE_DENSE : KNN_TABLE_HASH;
+        if (table == KNN_TABLE_DENSE && space + 1ull > 0x7fffffffull) {
+            set_err("knn_build: a dense table over %llu cells is too large; use KNN_TABLE_HASH",
+                    space);
+            return fail(KNN_EINVAL);
+        }
+        x->table = table;
+
+        // ---- Eq. 1 keys, stable sort by cell, cell offsets, table, row gather ----
+        unsigned long long *ka = nullptr, *kb = nullptr;
+        unsigned int *va = nullptr, *vb = nullptr;
+        void* rtmp = nullptr;
+        unsigned int *flags = nullptr, *cid = nullptr;
+        void* stmp = nullptr;
+        unsigned long long* cell_key = nullptr;
+        unsigned int* cell_start = nullptr;
+        st = tmp.alloc(&ka, (size_t)n, "keys");
+        if (st == KNN_OK) st = tmp.alloc(&kb, (size_t)n, "keys");
+        if (st == KNN_OK) st = dalloc(&va, (size_t)n, s, "row ids");
+        if (st == KNN_OK) st = dalloc(&vb, (size_t)n, s, "row ids");
+        if (st == KNN_OK) st = tmp.alloc(reinterpret_cast<char**>(&rtmp), radix_temp_bytes(n), "sort temp");
+        if (st != KNN_OK) {
+            dfree(va, s);
+            dfree(vb, s);
+            return fail(st);
+        }
+        unsigned long long* sk = nullptr;
+        unsigned int* sv = nullptr;
+        e = launch_cell_keys(pts, n, g, ka, va, s);
+        g_timer.mark("keys", s);
+        if (e == cudaSuccess) e = radix_sort_pairs(ka, va, kb, vb, n, bits, rtmp, &sk, &sv, s);
+        g_timer.mark("sort", s);
+        if (e != cudaSuccess) {
+            dfree(va, s);
+            dfree(vb, s);
+            return fail(cuda_fail(e, "sort by cell"));
+        }
+        // the sorted values are the training index of every row, in cell order
+        x->rid = sv;
+        if (sv == va)
+            dfree(vb, s);
+        else
+            dfree(va, s);
+
+        const unsigned long long scan_n =
+            table == KNN_TABLE_DENSE && space + 1ull > (unsigned long long)n ? space + 1ull
+                                                                           : (unsigned long long)n;
+        st = tmp.alloc(&flags, (size_t)n, "cell flags");
+        if (st == KNN_OK) st = tmp.alloc(&cid, (size_t)n, "cell ids");
+        if (st == KNN_OK) st = tmp.alloc(reinterpret_cast<char**>(&stmp), scan_temp_bytes((long long)scan_n), "scan temp");
+        if (st == KNN_OK) st = tmp.alloc(&cell_key, (size_t)n, "cell keys");
+        if (st == KNN_OK) st = tmp.alloc(&cell_start, (size_t)n + 1, "cell starts");
+        if (st == KNN_OK) st = dalloc(&x->gdev, 1, s, "grid");
+        if (st != KNN_OK) {
+            return fail(st);
+        }
+        e = launch_cells(sk, n, flags, cid, stmp, cell_key, cell_start, x->gdev, s);
+        if (e != cudaSuccess) {
+            return fail(cuda_fail(e, "cells"));
+        }
+        g_timer.mark("cells", s);
+        if (table == KNN_TABLE_DENSE) {
+            st = dalloc(&x->dstart, (size_t)space + 1, s, "dense table");
+            if (st != KNN_OK) {
+                return fail(st);
+            }
+            e = launch_dense_table(cell_key, cell_start, x->gdev, space, x->dstart, stmp, s);
+        } else {
+            unsigned long long cap = 16ull;
+            while (cap < 2ull * (unsigned long long)n) cap <<= 1;
+            x->max_slots = cap;
+            st = dalloc(&x->slots, (size_t)cap, s, "hash table");
+            if (st != KNN_OK) {
+                return fail(st);
+            }
+            e = launch_hash_table(cell_key, cell_start, x->gdev, x->slots, cap, s);
+        }
+        if (e != cudaSuccess) {
+            return fail(cuda_fail(e, "cell table"));
+        }
+        g_timer.mark("table", s);
+        st = dalloc(&x->rows, (size_t)n * row_floats(d), s, "rows");
+        if (st == KNN_OK && lab_in) st = dalloc(&x->labels, (size_t)n, s, "labels");
+        if (st != KNN_OK) {
+            return fail(st);
+        }
+        e = launch_gather(pts, n, d, x->rid, x->rows, s);
+        if (e == cudaSuccess && lab_in)
+            e = cudaMemcpyAsync(x->labels, lab_in, (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
+        g_timer.mark("gather", s);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x->last_use, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(x->last_use, s);
+        if (e != cudaSuccess) {
+            return fail(cuda_fail(e, "gather"));
+        }
+    }  // temporaries are freed here, ordered on the stream
+    *out = x;
+    return KNN_OK;
+}
+
+knn_status query_impl(const ghn_index* x, const float* queries_user, long long m, int k, int mode,
+                      int* ids_user, float* dist2_user, void* pred_user, long long* stats_user,
+                      int flags, cudaStream_t s)
+{
+    DeviceGuard dg(x->device);
+    const int d = x->d;
+    knn_status st = KNN_OK;
+    unsigned int status_host = 0u;
+    bool host_out = false;
+    g_timer.begin(s);
+    {
+        Temps tmp(s);
+        float* q = nullptr;
+        int* ids = nullptr;
+        float* dist2 = nullptr;
+        unsigned int* pred = nullptr;
+        long long* stats = nullptr;
+        st = device_view(queries_user, (size_t)(m * d), true, tmp, &q, "queries");
+        if (st == KNN_OK) st = device_view(ids_user, (size_t)(m * k), false, tmp, &ids, "ids");
+        if (st == KNN_OK) st = device_view(dist2_user, (size_t)(m * k), false, tmp, &dist2, "dist2");
+        if (st == KNN_OK && mode >= 0)
+            st = device_view(static_cast<unsigned int*>(pred_user), (size_t)m, false, tmp, &pred, "pred");
+        if (st == KNN_OK) st = device_view(stats_user, (size_t)(m * 3), false, tmp, &stats, "stats");
+        if (st != KNN_OK) return st;
+        host_out = ids != ids_user || (dist2_user && dist2 != dist2_user) ||
+                   (mode >= 0 && pred_user && (void*)pred != pred_user) ||
+                   (stats_user && stats != stats_user);
+
+        g_timer.mark("stage", s);
+        // scratch: work counter and status word
+        unsigned long long* scratch = nullptr;
+        st = tmp.alloc(&scratch, 2, "query scratch");
+        if (st != KNN_OK) return st;
+        GHN_CHECK(cudaMemsetAsync(scratch, 0, 2 * sizeof(unsigned long long), s), "memset");
+
+        const unsigned int* order = nullptr;
+        if ((flags & KNN_QUERY_SORTED) && m > 1 && x->key_bits > 0) {
+            unsigned long long *ka = nullptr, *kb = nullptr;
+            unsigned int *va = nullptr, *vb = nullptr;
+            char* rtmp = nullptr;
+            st = tmp.alloc(&ka, (size_t)m, "query keys");
+            if (st == KNN_OK) st = tmp.alloc(&kb, (size_t)m, "query keys");
+            if (st == KNN_OK) st = tmp.alloc(&va, (size_t)m, "query order");
+            if (st == KNN_OK) st = tmp.alloc(&vb, (size_t)m, "query order");
+            if (st == KNN_OK) st = tmp.alloc(&rtmp, radix_temp_bytes(m), "sort temp");
+            if (st != KNN_OK) return st;
+            unsigned long long* sk;
+            unsigned int* sv;
+            GHN_CHECK(launch_query_keys(q, m, x->g, ka, va, s), "query keys");
+            GHN_CHECK(radix_sort_pairs(ka, va, kb, vb, m, x->key_bits, rtmp, &sk, &sv, s),
+                      "query order");
+            order = sv;
+        }
+
+        g_timer.mark("order", s);
+        QueryArgs a;
+        memset(&a, 0, sizeof(a));
+        a.g = x->g;
+        a.q = q;
+        a.m = m;
+        a.k = k;
+        a.mode = mode;
+        a.ids = ids;
+        a.dist2 = dist2;
+        a.pred = pred;
+        a.rows = x->rows;
+        a.rid = x->rid;
+        a.labels = x->labels;
+        a.dstart = x->dstart;
+        a.slots = x->slots;
+        a.gdev = x->gdev;
+        a.counter = scratch;
+        a.status = reinterpret_cast<unsigned int*>(scratch + 1);
+        a.stats = stats;
+        a.order = order;
+        a.max_layers = max_layers_env();
+        a.dense = x->table == KNN_TABLE_DENSE;
+        GHN_CHECK(launch_query(a, num_sms(x->device), s), "query kernel");
+        g_timer.mark("search", s);
+
+        if (ids != ids_user)
+            GHN_CHECK(cudaMemcpyAsync(ids_user, ids, (size_t)(m * k) * 4, cudaMemcpyDeviceToHost, s), "ids");
+        if (dist2_user && dist2 != dist2_user)
+            GHN_CHECK(cudaMemcpyAsync(dist2_user, dist2, (size_t)(m * k) * 4, cudaMemcpyDeviceToHost, s), "dist2");
+        if (mode >= 0 && pred_user && (void*)pred != pred_user)
+            GHN_CHECK(cudaMemcpyAsync(pred_user, pred, (size_t)m * 4, cudaMemcpyDeviceToHost, s), "pred");
+        if (stats_user && stats != stats_user)
+            GHN_CHECK(cudaMemcpyAsync(stats_user, stats, (size_t)(m * 3) * 8, cudaMemcpyDeviceToHost, s), "stats");
+        if ((flags & KNN_QUERY_CHECKED) || stats_user)
+            GHN_CHECK(cudaMemcpyAsync(&status_host, scratch + 1, 4, cudaMemcpyDeviceToHost, s), "status");
+        g_timer.mark("copy", s);
+        GHN_CHECK(cudaEventRecord(x->last_use, s), "event");
+    }
+    if (host_out || (flags & KNN_QUERY_CHECKED) || stats_user)
+        GHN_CHECK(cudaStreamSynchronize(s), "synchronize");
+    if ((flags & KNN_QUERY_CHECKED) || stats_user) {
+        if (status_host & kStatusNonFinite) {
+            set_err("knn_query: a query coordinate is not finite");
+            return KNN_EINVAL;
+        }
+        if (status_host & kStatusLimit) {
+            set_err("knn_query: a query reached the layer cap");
+            return KNN_ELIMIT;
+        }
+    }
+    return KNN_OK;
+}
+
+knn_status check_query_args(const ghn_index* x, const float* queries, long long m, int k, int mode,
+                            const int* ids, const void* pred)
+{
+    if (!x) {
+        set_err("knn_query: index is NULL");
+        return KNN_EINVAL;
+    }
+    if (m < 0 || m >= (1ll << 31)) {
+        set_err("knn_query: m = %lld outside [0, 2^31)", m);
+        return KNN_EINVAL;
+    }
+    if (k < 1 || k > kMaxK) {
+        set_err("knn_query: k = %d outside [1, %d]", k, kMaxK);
+        return KNN_EINVAL;
+    }
+    if (mode < -1 || mode > 1) {
+        set_err("knn_query: unknown mode %d", mode);
+        return KNN_EINVAL;
+    }
+    if (mode >= 0 && !x->labels) {
+        set_err("knn_query: a prediction needs labels, and the index has none");
+        return KNN_EINVAL;
+    }
+    if (m > 0 && (!queries || !ids)) {
+        set_err("knn_query: queries and ids must not be NULL");
+        return KNN_EINVAL;
+    }
+    if (m > 0 && mode >= 0 && !pred) {
+        set_err("knn_query: pred must not be NULL for a prediction");
+        return KNN_EINVAL;
+    }
+    return KNN_OK;
+}
+
+}  // namespace
+
+namespace ghn {
+
+void count_launches(long long k) { g_launches += k; }
+
+cudaError_t launch_query(const QueryArgs& a, int sms, cudaStream_t s)
+{
+    // persistent grid: two 256-thread blocks per SM, fewer when m is small
+    long long blocks = (long long)sms * 2;
+    const long long need = (a.m + 7) / 8;
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    const int d = a.g.d;
+    count_launches(1);
+    if (d <= 2) return launch_query_d12(a, (int)blocks, s);
+    if (d <= 4) return launch_query_d34(a, (int)blocks, s);
+    if (d <= 6) return launch_query_d56(a, (int)blocks, s);
+    return launch_query_d78(a, (int)blocks, s);
+}
+
+}  // namespace ghn
+
+extern "C" {
+
+knn_status knn_build(const float* points, const void* labels, int64_t n, int32_t d,
+                     float cell_width, int32_t table, void* stream, ghn_index** out)
+{
+    if (!out) {
+        set_err("knn_build: out is NULL");
+        return KNN_EINVAL;
+    }
+    *out = nullptr;
+    if (!points) {
+        set_err("knn_build: points is NULL");
+        return KNN_EINVAL;
+    }
+    if (n < 1 || n >= (1ll << 31)) {
+        set_err("knn_build: n = %lld outside [1, 2^31)", (long long)n);
+        return KNN_EINVAL;
+    }
+    if (d < 1 || d > kMaxD) {
+        set_err("knn_build: d = %d outside [1, %d]", d, kMaxD);
+        return KNN_EINVAL;
+    }
+    if (!(cell_width > 0.0f) || !isfinite(cell_width)) {
+        set_err("knn_build: cell width must be a positive finite number");
+        return KNN_EINVAL;
+    }
+    if (table < KNN_TABLE_AUTO || table > KNN_TABLE_HASH) {
+        set_err("knn_build: unknown table kind %d", table);
+        return KNN_EINVAL;
+    }
+    return build_impl(points, labels, n, d, cell_width, table, static_cast<cudaStream_t>(stream),
+                      out);
+}
+
+knn_status knn_query(const ghn_index* index, const float* queries, int64_t m, int32_t k,
+                     int32_t mode, int32_t* ids, float* dist2, void* pred, int32_t flags,
+                     void* stream)
+{
+    knn_status st = check_query_args(index, queries, m, k, mode, ids, pred);
+    if (st != KNN_OK) return st;
+    if (m == 0) return KNN_OK;
+    return query_impl(index, queries, m, k, mode, ids, dist2, mode >= 0 ? pred : nullptr, nullptr,
+                      flags, static_cast<cudaStream_t>(stream));
+}
+
+knn_status knn_query_stats(const ghn_index* index, const float* queries, int64_t m, int32_t k,
+                           int32_t* ids, float* dist2, int64_t* stats, void* stream)
+{
+    knn_status st = check_query_args(index, queries, m, k, -1, ids, nullptr);
+    if (st != KNN_OK) return st;
+    if (m > 0 && !stats) {
+        set_err("knn_query_stats: stats must not be NULL");
+        return KNN_EINVAL;
+    }
+    if (m == 0) return KNN_OK;
+    return query_impl(index, queries, m, k, -1, ids, dist2, nullptr,
+                      reinterpret_cast<long long*>(stats), 0, static_cast<cudaStream_t>(stream));
+}
+
+knn_status knn_index_info(const ghn_index* index, knn_index_info_t* info)
+{
+    if (!index || !info) {
+        set_err("knn_index_info: NULL argument");
+        return KNN_EINVAL;
+    }
+    ghn_index* x = const_cast<ghn_index*>(index);
+    if (!x->info_ready) {
+        DeviceGuard dg(x->device);
+        GHN_CHECK(cudaEventSynchronize(x->last_use), "synchronize");
+        GHN_CHECK(cudaMemcpy(&x->host_gdev, x->gdev, sizeof(GridDev), cudaMemcpyDeviceToHost),
+                  "read grid");
+        x->info_ready = true;
+    }
+    memset(info, 0, sizeof(*info));
+    info->n = x->n;
+    info->d = x->d;
+    info->table = x->table;
+    info->cell_width = x->w;
+    for (int j = 0; j < x->d; ++j) {
+        info->origin[j] = x->g.lo[j];
+        info->extent[j] = x->g.cmax[j] + 1;
+    }
+    info->num_cells = (int64_t)x->host_gdev.ncells;
+    info->table_slots = x->table == KNN_TABLE_DENSE ? (int64_t)x->ncell_space + 1
+                                                    : (int64_t)(x->host_gdev.hmask + 1ull);
+    info->row_floats = row_floats(x->d);
+    info->has_labels = x->labels != nullptr;
+    return KNN_OK;
+}
+
+knn_status knn_index_export(const ghn_index* index, uint64_t* cell_keys, uint32_t* cell_start,
+                            int32_t* rows)
+{
+    knn_index_info_t info;
+    knn_status st = knn_index_info(index, &info);
+    if (st != KNN_OK) return st;
+    const ghn_index* x = index;
+    DeviceGuard dg(x->device);
+    GHN_CHECK(cudaDeviceSynchronize(), "synchronize");
+    const long long n = x->n, u = info.num_cells;
+    if (rows) GHN_CHECK(cudaMemcpy(rows, x->rid, (size_t)n * 4, cudaMemcpyDeviceToHost), "rows");
+    if (!cell_keys && !cell_start) return KNN_OK;
+    // rebuild the cell list from the table
+    uint64_t* keys = cell_keys;
+    uint32_t* starts = cell_start;
+    uint64_t* kbuf = nullptr;
+    uint32_t* sbuf = nullptr;
+    if (!keys) keys = kbuf = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(u > 0 ? u : 1));
+    if (!starts) starts = sbuf = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(u + 1));
+    if (!keys || !starts) {
+        free(kbuf);
+        free(sbuf);
+        set_err("knn_index_export: out of host memory");
+        return KNN_ENOMEM;
+    }
+    long long c = 0;
+    if (x->table == KNN_TABLE_DENSE) {
+        const size_t cnt = (size_t)x->ncell_space + 1;
+        uint32_t* ds = (uint32_t*)malloc(sizeof(uint32_t) * cnt);
+        if (!ds) {
+            free(kbuf);
+            free(sbuf);
+            set_err("knn_index_export: out of host memory");
+            return KNN_ENOMEM;
+        }
+        cudaError_t e = cudaMemcpy(ds, x->dstart, sizeof(uint32_t) * cnt, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            free(ds);
+            free(kbuf);
+            free(sbuf);
+            return cuda_fail(e, "read table");
+        }
+        for (unsigned long long id = 0; id < x->ncell_space; ++id) {
+            if (ds[id + 1] > ds[id] && c < u) {
+                keys[c] = id;
+                starts[c] = ds[id];
+                ++c;
+            }
+        }
+        free(ds);
+    } else {
+        const size_t cap = (size_t)(x->host_gdev.hmask + 1ull);
+        HashSlot* hs = (HashSlot*)malloc(sizeof(HashSlot) * cap);
+        if (!hs) {
+            free(kbuf);
+            free(sbuf);
+            set_err("knn_index_export: out of host memory");
+            return KNN_ENOMEM;
+        }
+        cudaError_t e = cudaMemcpy(hs, x->slots, sizeof(HashSlot) * cap, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            free(hs);
+            free(kbuf);
+            free(sbuf);
+            return cuda_fail(e, "read table");
+        }
+        for (size_t i = 0; i < cap; ++i) {
+            if (hs[i].key != kEmptyKey && c < u) {
+                keys[c] = hs[i].key;
+                starts[c] = hs[i].start;
+                ++c;
+            }
+        }
+        // order the occupied slots by cell id
+        struct P {
+            uint64_t k;
+            uint32_t s;
+        };
+        P* ps = (P*)malloc(sizeof(P) * (size_t)(c > 0 ? c : 1));
+        if (!ps) {
+            free(hs);
+            free(kbuf);
+            free(sbuf);
+            set_err("knn_index_export: out of host memory");
+            return KNN_ENOMEM;
+        }
+        for (long long i = 0; i < c; ++i) ps[i] = P{keys[i], starts[i]};
+        qsort(ps, (size_t)c, sizeof(P), [](const void* a, const void* b) {
+            const uint64_t x1 = ((const P*)a)->k, x2 = ((const P*)b)->k;
+            return x1 < x2 ? -1 : (x1 > x2 ? 1 : 0);
+        });
+        for (long long i = 0; i < c; ++i) {
+            keys[i] = ps[i].k;
+            starts[i] = ps[i].s;
+        }
+        free(ps);
+        free(hs);
+    }
+    starts[c] = (uint32_t)n;
+    free(kbuf);
+    free(sbuf);
+    if (c != u) {
+        set_err("knn_index_export: table holds %lld cells, expected %lld", c, u);
+        return KNN_ECUDA;
+    }
+    return KNN_OK;
+}
+
+knn_status knn_timing_enable(int32_t on)
+{
+    g_timing_on = on ? 1 : 0;
+    return KNN_OK;
+}
+
+int32_t knn_timing_read(const char** names, float* ms, int32_t cap)
+{
+    PhaseTimer& t = g_timer;
+    if (!t.active || t.count == 0) return 0;
+    if (cudaEventSynchronize(t.ev[t.count]) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    const int n = t.count < cap ? t.count : cap;
+    for (int i = 0; i < n; ++i) {
+        if (names) names[i] = t.names[i];
+        if (ms) {
+            float v = 0.0f;
+            cudaEventElapsedTime(&v, t.ev[i], t.ev[i + 1]);
+            ms[i] = v;
+        }
+    }
+    return t.count;
+}
+
+int64_t knn_kernel_launches(void) { return g_launches.load(); }
+
+void knn_free(ghn_index* index) { free_index(index); }
+
+const char* knn_last_error(void) { return g_err; }
+
+int32_t knn_abi_version(void) { return 1; }
+
+}  // extern "C"

@@ -1,0 +1,139 @@
+// Internal declarations of the GB300 grid-hashing KNN library (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ghn {
+
+constexpr int kMaxD = 8;
+constexpr int kMaxK = 64;
+constexpr unsigned long long kEmptyKey = ~0ull;
+constexpr float kQueryClamp = 1099511627776.0f;  // 2^40
+
+// Status bits a kernel ORs into a device word.
+constexpr unsigned int kStatusNonFinite = 1u;  // a non-finite point or query
+constexpr unsigned int kStatusLimit = 2u;      // a query reached the layer cap
+constexpr unsigned int kStatusExtent = 4u;     // too many cells along one dimension
+
+// Grid geometry, passed by value to the kernels.
+struct GridConst {
+    float lo[kMaxD];                 // origin: per-dimension minimum
+    float w;                         // cell width
+    int d;
+    long long cmax[kMaxD];           // largest occupied cell coordinate (extent - 1)
+    unsigned long long stride[kMaxD];  // linear id = sum c_j * stride_j, stride_{d-1} = 1
+};
+
+// Results of the build that only the device knows without a sync.
+struct GridDev {
+    unsigned long long ncells;  // occupied cells U
+    unsigned long long hmask;   // hash capacity - 1 (capacity: power of two >= 2U)
+};
+
+// Box of the training points, read back once by the host during build.
+struct BoxOut {
+    float lo[kMaxD];
+    float hi[kMaxD];
+    long long ext[kMaxD];
+    unsigned int flags;
+    unsigned int pad;
+};
+
+// One open-addressing slot: a linear cell id and its row range [start, end).
+struct __align__(16) HashSlot {
+    unsigned long long key;
+    unsigned int start;
+    unsigned int end;
+};
+
+// SplitMix64 finaliser (Steele, Lea, Flood 2014; constants as published by
+// Vigna): a 64-bit bijective mixer used to spread cell ids over the table.
+__host__ __device__ __forceinline__ unsigned long long mix64(unsigned long long z)
+{
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+// Floats per stored row: 2 for d <= 2, 4 for d <= 4, 8 otherwise.
+__host__ __device__ constexpr int row_floats(int d) { return d <= 2 ? 2 : (d <= 4 ? 4 : 8); }
+
+// Count of kernels launched by this library (read by knn_kernel_launches).
+void count_launches(long long k);
+
+// ---- build launchers (build_kernels.cu) ----
+cudaError_t launch_box(const float* pts, long long n, int d, float w, float* partial,
+                       int partial_blocks, BoxOut* out, cudaStream_t s);
+int box_partial_blocks(long long n);
+
+cudaError_t launch_cell_keys(const float* pts, long long n, const GridConst& g,
+                             unsigned long long* keys, unsigned int* vals, cudaStream_t s);
+
+// LSD radix sort of (key, value) by the low `bits` bits of the key; stable.
+// Returns in *result_keys / *result_vals the buffers that hold the sorted data.
+size_t radix_temp_bytes(long long n);
+cudaError_t radix_sort_pairs(unsigned long long* keys_a, unsigned int* vals_a,
+                             unsigned long long* keys_b, unsigned int* vals_b, long long n,
+                             int bits, void* temp, unsigned long long** result_keys,
+                             unsigned int** result_vals, cudaStream_t s);
+
+// Exclusive prefix sum of n uint32 values (out may alias in).
+size_t scan_temp_bytes(long long n);
+cudaError_t scan_exclusive(const unsigned int* in, unsigned int* out, long long n, void* temp,
+                           cudaStream_t s);
+
+cudaError_t launch_cells(const unsigned long long* sorted_keys, long long n,
+                         unsigned int* flags_tmp, unsigned int* cid_tmp, void* scan_tmp,
+                         unsigned long long* cell_key, unsigned int* cell_start, GridDev* gdev,
+                         cudaStream_t s);
+
+// Dense table: dstart[id] = first row of cell id, for every id of the box, and
+// dstart[ncell_space] = n.  scan_tmp: scan_temp_bytes(ncell_space + 1).
+cudaError_t launch_dense_table(const unsigned long long* cell_key, const unsigned int* cell_start,
+                               const GridDev* gdev, unsigned long long ncell_space,
+                               unsigned int* dstart, void* scan_tmp, cudaStream_t s);
+
+cudaError_t launch_hash_table(const unsigned long long* cell_key, const unsigned int* cell_start,
+                              const GridDev* gdev, HashSlot* slots, unsigned long long max_slots,
+                              cudaStream_t s);
+
+cudaError_t launch_gather(const float* pts, long long n, int d, const unsigned int* order,
+                          float* rows, cudaStream_t s);
+
+// ---- query ----
+struct QueryArgs {
+    GridConst g;
+    const float* q;                 // m*d queries
+    long long m;
+    int k;
+    int mode;                       // -1 none, 0 vote, 1 mean
+    int* ids;                       // m*k
+    float* dist2;                   // m*k or null
+    void* pred;                     // m or null
+    const float* rows;              // n rows of row_floats(d) floats, cell order
+    const unsigned int* rid;        // n training indices, cell order
+    const unsigned int* labels;     // n raw 32-bit outputs, training order, or null
+    const unsigned int* dstart;     // dense: ncell_space + 1 row offsets
+    const HashSlot* slots;          // hash table
+    const GridDev* gdev;
+    unsigned long long* counter;    // work counter, zero at launch
+    unsigned int* status;           // status bits
+    long long* stats;               // m*3 or null (exhaustive counting walk)
+    const unsigned int* order;      // visiting order of queries or null
+    long long max_layers;           // 0 = no cap
+    int dense;
+};
+
+cudaError_t launch_query(const QueryArgs& a, int num_sms, cudaStream_t s);
+
+cudaError_t launch_query_d12(const QueryArgs& a, int blocks, cudaStream_t s);
+cudaError_t launch_query_d34(const QueryArgs& a, int blocks, cudaStream_t s);
+cudaError_t launch_query_d56(const QueryArgs& a, int blocks, cudaStream_t s);
+cudaError_t launch_query_d78(const QueryArgs& a, int blocks, cudaStream_t s);
+
+// Query keys for the locality order (cell id of each query, clamped into the box).
+cudaError_t launch_query_keys(const float* q, long long m, const GridConst& g,
+                              unsigned long long* keys, unsigned int* vals, cudaStream_t s);
+
+}  // namespace ghn

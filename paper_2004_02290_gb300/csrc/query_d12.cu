@@ -1,0 +1,16 @@
+// Query kernel instances for d = 1 and d = 2 (one translation unit per pair,
+// so the build compiles them in parallel).
+#include "query_kernel.cuh"
+
+namespace ghn {
+
+cudaError_t launch_query_d12(const QueryArgs& a, int blocks, cudaStream_t s)
+{
+    switch (a.g.d) {
+    case 1: return qk::launch_d<1>(a, blocks, s);
+    case 2: return qk::launch_d<2>(a, blocks, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace ghn

@@ -1,0 +1,16 @@
+// Query kernel instances for d = 3 and d = 4 (one translation unit per pair,
+// so the build compiles them in parallel).
+#include "query_kernel.cuh"
+
+namespace ghn {
+
+cudaError_t launch_query_d34(const QueryArgs& a, int blocks, cudaStream_t s)
+{
+    switch (a.g.d) {
+    case 3: return qk::launch_d<3>(a, blocks, s);
+    case 4: return qk::launch_d<4>(a, blocks, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace ghn

@@ -1,0 +1,16 @@
+// Query kernel instances for d = 7 and d = 8 (one translation unit per pair,
+// so the build compiles them in parallel).
+#include "query_kernel.cuh"
+
+namespace ghn {
+
+cudaError_t launch_query_d78(const QueryArgs& a, int blocks, cudaStream_t s)
+{
+    switch (a.g.d) {
+    case 7: return qk::launch_d<7>(a, blocks, s);
+    case 8: return qk::launch_d<8>(a, blocks, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace ghn

@@ -1,0 +1,256 @@
+"""Thin ctypes binding of the C ABI in ``include/ghn_knn.h``.
+
+Argument marshalling only: every step of index build and query runs in the
+CUDA library ``_build/libghn_knn.so``.  There is no fallback: if the library
+is missing, loading raises.  Arrays may be torch tensors (CUDA or CPU) or
+numpy arrays; host arrays are staged to the GPU by the library itself.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+KNN_OK, KNN_EINVAL, KNN_ENOMEM, KNN_ECUDA, KNN_ELIMIT = 0, 1, 2, 3, 4
+KNN_NONE, KNN_VOTE, KNN_MEAN = -1, 0, 1
+KNN_TABLE_AUTO, KNN_TABLE_DENSE, KNN_TABLE_HASH = 0, 1, 2
+KNN_QUERY_CHECKED, KNN_QUERY_SORTED = 1, 2
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libghn_knn.so")
+
+_lock = threading.Lock()
+_lib = None
+
+
+class KnnError(RuntimeError):
+    def __init__(self, code, message):
+        super().__init__(f"[status {code}] {message}")
+        self.code = code
+
+
+class knn_index_info_t(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int32), ("table", ctypes.c_int32),
+                ("cell_width", ctypes.c_float), ("origin", ctypes.c_float * 8),
+                ("extent", ctypes.c_int64 * 8), ("num_cells", ctypes.c_int64),
+                ("table_slots", ctypes.c_int64), ("row_floats", ctypes.c_int32),
+                ("has_labels", ctypes.c_int32)]
+
+
+EXPORTED = ["knn_build", "knn_query", "knn_query_stats", "knn_index_info", "knn_index_export",
+            "knn_timing_enable", "knn_timing_read", "knn_kernel_launches", "knn_free",
+            "knn_last_error", "knn_abi_version"]
+
+
+def library(path: str | None = None) -> ctypes.CDLL:
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"CUDA library not built: {p} is missing "
+                               "(run __graft_entry__.build() or build_ext.build())")
+        lib = ctypes.CDLL(p)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        lib.knn_build.argtypes = [vp, vp, i64, i32, ctypes.c_float, i32, vp, ctypes.POINTER(vp)]
+        lib.knn_build.restype = i32
+        lib.knn_query.argtypes = [vp, vp, i64, i32, i32, vp, vp, vp, i32, vp]
+        lib.knn_query.restype = i32
+        lib.knn_query_stats.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp]
+        lib.knn_query_stats.restype = i32
+        lib.knn_index_info.argtypes = [vp, ctypes.POINTER(knn_index_info_t)]
+        lib.knn_index_info.restype = i32
+        lib.knn_index_export.argtypes = [vp, vp, vp, vp]
+        lib.knn_index_export.restype = i32
+        lib.knn_free.argtypes = [vp]
+        lib.knn_free.restype = None
+        lib.knn_last_error.argtypes = []
+        lib.knn_last_error.restype = ctypes.c_char_p
+        lib.knn_abi_version.argtypes = []
+        lib.knn_abi_version.restype = i32
+        lib.knn_timing_enable.argtypes = [i32]
+        lib.knn_timing_enable.restype = i32
+        lib.knn_timing_read.argtypes = [ctypes.POINTER(ctypes.c_char_p),
+                                        ctypes.POINTER(ctypes.c_float), i32]
+        lib.knn_timing_read.restype = i32
+        lib.knn_kernel_launches.argtypes = []
+        lib.knn_kernel_launches.restype = i64
+        _lib = lib
+        return lib
+
+
+def _check(code: int):
+    if code != KNN_OK:
+        raise KnnError(code, library().knn_last_error().decode(errors="replace"))
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a):
+    """(address, keepalive) of a contiguous torch tensor or numpy array, or (None, None)."""
+    if a is None:
+        return None, None
+    if _is_torch(a):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr(), a
+    arr = np.ascontiguousarray(a)
+    return arr.ctypes.data, arr
+
+
+def _stream(stream, *arrays):
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    for a in arrays:
+        if a is not None and _is_torch(a) and a.is_cuda:
+            import torch
+            return torch.cuda.current_stream(a.device).cuda_stream
+    return None
+
+
+def _check_f32(a, name):
+    dt = str(a.dtype)
+    if not dt.endswith("float32"):
+        raise ValueError(f"{name} must be float32, got {dt}")
+
+
+class Index:
+    """A built GHN index (device memory owned by the library)."""
+
+    def __init__(self, handle: ctypes.c_void_p, n: int, d: int):
+        self._h = handle
+        self.n = n
+        self.d = d
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    def info(self) -> knn_index_info_t:
+        out = knn_index_info_t()
+        _check(library().knn_index_info(self._h, ctypes.byref(out)))
+        return out
+
+    def export(self):
+        """(cell_keys uint64, cell_start uint32, rows int32) as numpy arrays."""
+        inf = self.info()
+        u = int(inf.num_cells)
+        keys = np.zeros(u, np.uint64)
+        starts = np.zeros(u + 1, np.uint32)
+        rows = np.zeros(self.n, np.int32)
+        _check(library().knn_index_export(self._h, keys.ctypes.data, starts.ctypes.data,
+                                          rows.ctypes.data))
+        return keys, starts, rows
+
+    def query(self, queries, k: int, mode: int = KNN_NONE, flags: int = 0, stream=None,
+              ids=None, dist2=None, pred=None, want_dist2: bool = True):
+        return knn_query(self, queries, k, mode, flags=flags, stream=stream, ids=ids,
+                         dist2=dist2, pred=pred, want_dist2=want_dist2)
+
+    def query_stats(self, queries, k: int, stream=None):
+        return knn_query_stats(self, queries, k, stream=stream)
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            library().knn_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def knn_build(points, labels=None, cell_width: float = 1.0, table: int = KNN_TABLE_AUTO,
+              stream=None) -> Index:
+    """Cell sampling (Sec. III.A): returns an Index over n x d float32 points."""
+    if points.ndim != 2:
+        raise ValueError("points must be n x d")
+    _check_f32(points, "points")
+    n, d = int(points.shape[0]), int(points.shape[1])
+    pp, keep_p = _ptr(points)
+    lp, keep_l = _ptr(labels)
+    if labels is not None and (labels.shape[0] != n or np.dtype(str(labels.dtype).split(".")[-1]).itemsize != 4):
+        raise ValueError("labels must be n 32-bit values")
+    h = ctypes.c_void_p()
+    _check(library().knn_build(pp, lp, n, d, ctypes.c_float(float(np.float32(cell_width))),
+                               table, _stream(stream, points, labels), ctypes.byref(h)))
+    del keep_p, keep_l
+    return Index(h, n, d)
+
+
+def _alloc_like(ref, shape, dtype_name):
+    if ref is not None and _is_torch(ref):
+        import torch
+        return torch.empty(shape, dtype=getattr(torch, dtype_name), device=ref.device)
+    return np.empty(shape, dtype=dtype_name)
+
+
+def knn_query(index: Index, queries, k: int, mode: int = KNN_NONE, flags: int = 0, stream=None,
+              ids=None, dist2=None, pred=None, want_dist2: bool = True):
+    """Exploration + prediction (Sec. III.B, Sec. I): returns (ids, dist2, pred)."""
+    if queries.ndim != 2 or queries.shape[1] != index.d:
+        raise ValueError("queries must be m x d")
+    _check_f32(queries, "queries")
+    m = int(queries.shape[0])
+    if ids is None:
+        ids = _alloc_like(queries, (m, k), "int32")
+    if dist2 is None and want_dist2:
+        dist2 = _alloc_like(queries, (m, k), "float32")
+    if pred is None and mode >= 0:
+        pred = _alloc_like(queries, (m,), "int32" if mode == KNN_VOTE else "float32")
+    qp, kq = _ptr(queries)
+    ip, ki = _ptr(ids)
+    dp, kd = _ptr(dist2)
+    pp, kp = _ptr(pred)
+    _check(library().knn_query(index._h, qp, m, k, mode, ip, dp, pp, flags,
+                               _stream(stream, queries, ids)))
+    del kq, ki, kd, kp
+    return ids, dist2, pred
+
+
+def knn_query_stats(index: Index, queries, k: int, stream=None):
+    """Walk without skipping; returns (ids, dist2, stats m x 3 int64)."""
+    m = int(queries.shape[0])
+    ids = _alloc_like(queries, (m, k), "int32")
+    dist2 = _alloc_like(queries, (m, k), "float32")
+    stats = _alloc_like(queries, (m, 3), "int64")
+    qp, kq = _ptr(queries)
+    ip, ki = _ptr(ids)
+    dp, kd = _ptr(dist2)
+    sp, ks = _ptr(stats)
+    _check(library().knn_query_stats(index._h, qp, m, k, ip, dp, sp,
+                                     _stream(stream, queries, ids)))
+    del kq, ki, kd, ks
+    return ids, dist2, stats
+
+
+def knn_free(index: Index):
+    index.free()
+
+
+def knn_timing_enable(on: bool = True):
+    _check(library().knn_timing_enable(1 if on else 0))
+
+
+def knn_timing_read() -> list[tuple[str, float]]:
+    """Phases of the last build / query on this thread: [(name, device ms)]."""
+    names = (ctypes.c_char_p * 16)()
+    ms = (ctypes.c_float * 16)()
+    cnt = library().knn_timing_read(names, ms, 16)
+    return [(names[i].decode(), float(ms[i])) for i in range(min(cnt, 16))]
+
+
+def knn_kernel_launches() -> int:
+    return int(library().knn_kernel_launches())
+
+
+def knn_last_error() -> str:
+    return library().knn_last_error().decode(errors="replace")

@@ -1,0 +1,364 @@
+"""Parity of the CUDA path with the CPU oracle, through the C ABI (GPU needed).
+
+Neighbour ids, squared distances and votes must be bit-exact; means must be
+within 1e-6 relative (and are expected bit-exact: both sides sum the same
+floats in double precision in the same order).  Small cases compare every
+output; the full-size workloads compare a seeded sample of queries.
+"""
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_2004_02290_gb300 import knn
+from paper_2004_02290_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+MEAN_RTOL = 1e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+
+    __graft_entry__.build()
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def gpu_run(points, labels, queries, w, k, mode, table=knn.KNN_TABLE_AUTO, flags=0):
+    idx = knn.knn_build(_dev(points), None if labels is None else _dev(labels), w, table)
+    ids, d2, pred = idx.query(_dev(queries), k, mode, flags=flags | knn.KNN_QUERY_CHECKED)
+    torch.cuda.synchronize()
+    info = idx.info()
+    out = (ids.cpu().numpy(), d2.cpu().numpy(), None if pred is None else pred.cpu().numpy())
+    idx.free()
+    return out, info
+
+
+def oracle_run(points, labels, queries, w, k, mode):
+    g = oracle.Grid(points, labels, w)
+    return g.query(queries, k, mode)
+
+
+def assert_same(got, exp, mode):
+    ids, d2, pred = got
+    e_ids, e_d2, e_pred = exp
+    assert ids.shape == e_ids.shape
+    bad = np.nonzero((ids != e_ids).any(axis=1))[0]
+    assert bad.size == 0, f"{bad.size} rows differ, first {bad[:5]}: {ids[bad[0]]} vs {e_ids[bad[0]]}"
+    assert np.array_equal(d2.view(np.uint32), e_d2.view(np.uint32))
+    if mode == knn.KNN_VOTE:
+        assert np.array_equal(pred, e_pred)
+    elif mode == knn.KNN_MEAN:
+        rel = np.abs(pred.astype(np.float64) - e_pred) / np.maximum(np.abs(e_pred), 1e-30)
+        assert rel.max() <= MEAN_RTOL
+        assert np.array_equal(pred.view(np.uint32), e_pred.view(np.uint32))
+
+
+# ---- the tiny workload, every output ----
+
+@pytest.mark.parametrize("flags", [0, knn.KNN_QUERY_SORTED])
+@pytest.mark.parametrize("table", [knn.KNN_TABLE_DENSE, knn.KNN_TABLE_HASH])
+def test_tiny_workload(flags, table):
+    w = wl.make("tiny")
+    got, info = gpu_run(w.points, w.labels, w.queries, w.w, w.k, w.mode, table, flags)
+    assert info.table == table
+    assert_same(got, oracle_run(w.points, w.labels, w.queries, w.w, w.k, w.mode), w.mode)
+
+
+def test_tiny_index_matches_algorithm1():
+    """The built grid: the same occupied cells as the oracle, members in append order."""
+    w = wl.make("tiny")
+    for table in (knn.KNN_TABLE_DENSE, knn.KNN_TABLE_HASH):
+        idx = knn.knn_build(_dev(w.points), _dev(w.labels), w.w, table)
+        info = idx.info()
+        keys, starts, rows = idx.export()
+        idx.free()
+        g = oracle.Grid(w.points, w.labels, w.w)
+        o, cmax = g.origin()
+        assert np.array_equal(np.array(info.origin[:w.d], np.float32), o)
+        assert list(info.extent[:w.d]) == (cmax + 1).tolist()
+        coords, counts, members = g.cells()
+        assert info.num_cells == g.num_cells
+        ext = np.array(info.extent[:w.d], np.int64)
+        strides = np.array([int(np.prod(ext[j + 1:])) for j in range(w.d)], np.int64)
+        lin = (coords * strides).sum(axis=1)
+        order = np.argsort(lin)
+        assert np.array_equal(keys.astype(np.int64), lin[order])
+        assert starts[-1] == w.n
+        for c, e in enumerate(order):
+            assert np.array_equal(rows[starts[c]:starts[c + 1]], members[e])
+
+
+# ---- many shapes: d, k, tables, ties, outside queries ----
+
+CASES = [
+    # d, n, m, w, k, mode
+    (1, 3000, 400, 0.002, 7, knn.KNN_VOTE),
+    (2, 5000, 500, 0.02, 1, knn.KNN_VOTE),
+    (2, 5000, 500, 0.02, 33, knn.KNN_VOTE),
+    (3, 8000, 500, 0.05, 16, knn.KNN_MEAN),
+    (4, 8000, 400, 0.12, 10, knn.KNN_VOTE),
+    (4, 8000, 400, 0.12, 64, knn.KNN_MEAN),
+    (5, 4000, 200, 0.3, 5, knn.KNN_VOTE),
+    (6, 4000, 200, 0.35, 12, knn.KNN_MEAN),
+    (7, 3000, 150, 0.45, 3, knn.KNN_VOTE),
+    (8, 3000, 150, 0.5, 40, knn.KNN_VOTE),
+]
+
+
+@pytest.mark.parametrize("table", [knn.KNN_TABLE_DENSE, knn.KNN_TABLE_HASH])
+@pytest.mark.parametrize("d,n,m,w,k,mode", CASES)
+def test_uniform_cases(d, n, m, w, k, mode, table):
+    x, lab, q = wl.uniform(n, m, d, seed=1000 + 17 * d + k)
+    if mode == knn.KNN_MEAN:
+        lab = wl.regression_targets(x, seed=d)
+    # queries also outside the box and on cell boundaries
+    extra = np.stack([np.full(d, -0.3), np.full(d, 1.4), np.full(d, 0.5),
+                      np.full(d, np.float32(w) * 3)]).astype(np.float32)
+    q = np.concatenate([q, extra]).astype(np.float32)
+    got, info = gpu_run(x, lab, q, w, k, mode, table)
+    assert_same(got, oracle_run(x, lab, q, w, k, mode), mode)
+
+
+def test_lattice_ties():
+    """Integer lattice, w = 1: many exact distance ties, broken by the training index."""
+    x, lab, q = wl.lattice(24, 2, 500, seed=3)
+    for k in (1, 4, 9, 25, 64):
+        for table in (knn.KNN_TABLE_DENSE, knn.KNN_TABLE_HASH):
+            got, _ = gpu_run(x, lab, q, 1.0, k, knn.KNN_VOTE, table)
+            assert_same(got, oracle_run(x, lab, q, 1.0, k, knn.KNN_VOTE), knn.KNN_VOTE)
+
+
+def test_lattice_3d_half_width():
+    x, lab, q = wl.lattice(12, 3, 300, seed=4)
+    got, _ = gpu_run(x, lab, q, 0.5, 8, knn.KNN_VOTE, knn.KNN_TABLE_HASH)
+    assert_same(got, oracle_run(x, lab, q, 0.5, 8, knn.KNN_VOTE), knn.KNN_VOTE)
+
+
+def test_single_cell_and_duplicates():
+    """All points in one cell (w larger than the range), with exact duplicates."""
+    x, lab, q = wl.uniform(2000, 300, 3, seed=7)
+    x[500:900] = x[0]
+    for table in (knn.KNN_TABLE_DENSE, knn.KNN_TABLE_HASH):
+        got, info = gpu_run(x, lab, q, 5.0, 20, knn.KNN_VOTE, table)
+        assert info.num_cells == 1
+        assert_same(got, oracle_run(x, lab, q, 5.0, 20, knn.KNN_VOTE), knn.KNN_VOTE)
+
+
+def test_k_larger_than_n():
+    x, lab, q = wl.uniform(11, 40, 2, seed=8)
+    for k in (11, 12, 64):
+        got, _ = gpu_run(x, lab, q, 0.1, k, knn.KNN_VOTE)
+        assert_same(got, oracle_run(x, lab, q, 0.1, k, knn.KNN_VOTE), knn.KNN_VOTE)
+        assert (got[0][:, 11:] == -1).all() and np.isinf(got[1][:, 11:]).all()
+
+
+def test_one_point():
+    x = np.array([[0.25, -3.0]], np.float32)
+    q = np.array([[0.0, 0.0], [1e6, -1e6], [0.25, -3.0]], np.float32)
+    got, _ = gpu_run(x, np.array([5], np.int32), q, 0.7, 3, knn.KNN_VOTE)
+    assert_same(got, oracle_run(x, np.array([5], np.int32), q, 0.7, 3, knn.KNN_VOTE), knn.KNN_VOTE)
+
+
+def test_far_queries_clamped():
+    x, lab, _ = wl.uniform(3000, 1, 2, seed=9)
+    q = np.array([[1e30, 1e30], [-1e30, 0.5], [0.5, 3e9], [-7.0, -7.0]], np.float32)
+    got, _ = gpu_run(x, lab, q, 0.05, 6, knn.KNN_VOTE)
+    assert_same(got, oracle_run(x, lab, q, 0.05, 6, knn.KNN_VOTE), knn.KNN_VOTE)
+
+
+def test_clustered_heavy_cells():
+    """Tight clusters: cells with thousands of points next to near-empty space."""
+    w = wl.make("skewed_reg", n=200_000, m=3000, w=0.02)
+    got, _ = gpu_run(w.points, w.labels, w.queries, w.w, w.k, w.mode)
+    assert_same(got, oracle_run(w.points, w.labels, w.queries, w.w, w.k, w.mode), w.mode)
+
+
+def test_large_cls_shape_small():
+    w = wl.make("large_cls", n=100_000, m=5000, w=0.03)
+    got, info = gpu_run(w.points, w.labels, w.queries, w.w, w.k, w.mode, knn.KNN_TABLE_HASH,
+                        knn.KNN_QUERY_SORTED)
+    assert info.table == knn.KNN_TABLE_HASH
+    assert_same(got, oracle_run(w.points, w.labels, w.queries, w.w, w.k, w.mode), w.mode)
+
+
+# ---- counters of the method's work (exhaustive walk) ----
+
+@pytest.mark.parametrize("table", [knn.KNN_TABLE_DENSE, knn.KNN_TABLE_HASH])
+def test_stats_match_oracle(table):
+    w = wl.make("tiny")
+    idx = knn.knn_build(_dev(w.points), _dev(w.labels), w.w, table)
+    ids, d2, st = idx.query_stats(_dev(w.queries), w.k)
+    ids_q, d2_q, _ = idx.query(_dev(w.queries), w.k)
+    torch.cuda.synchronize()
+    g = oracle.Grid(w.points, w.labels, w.w)
+    e_ids, e_d2, _, e_st = g.query(w.queries, w.k, -1, stats=True)
+    assert np.array_equal(st.cpu().numpy(), e_st)
+    assert np.array_equal(ids.cpu().numpy(), e_ids)
+    # the skipping walk gives the same result as the exhaustive one
+    assert np.array_equal(ids_q.cpu().numpy(), e_ids)
+    assert np.array_equal(d2_q.cpu().numpy().view(np.uint32), e_d2.view(np.uint32))
+    idx.free()
+
+
+# ---- host buffers, empty and invalid input, determinism ----
+
+def test_host_buffers_match_device_buffers():
+    w = wl.make("tiny")
+    idx = knn.knn_build(w.points, w.labels, w.w)  # numpy: host pointers
+    ids, d2, pred = idx.query(w.queries, w.k, knn.KNN_VOTE)
+    assert isinstance(ids, np.ndarray)
+    assert_same((ids, d2, pred), oracle_run(w.points, w.labels, w.queries, w.w, w.k, w.mode),
+                knn.KNN_VOTE)
+    idx.free()
+
+
+def test_empty_query_batch():
+    w = wl.make("tiny")
+    idx = knn.knn_build(_dev(w.points), _dev(w.labels), w.w)
+    ids, d2, pred = idx.query(_dev(np.zeros((0, 2), np.float32)), 5, knn.KNN_VOTE,
+                              flags=knn.KNN_QUERY_CHECKED)
+    assert ids.shape == (0, 5)
+    idx.free()
+
+
+def test_non_finite_query_is_reported():
+    w = wl.make("tiny")
+    idx = knn.knn_build(_dev(w.points), _dev(w.labels), w.w)
+    q = w.queries[:10].copy()
+    q[3, 1] = np.nan
+    with pytest.raises(knn.KnnError) as e:
+        idx.query(_dev(q), 5, knn.KNN_VOTE, flags=knn.KNN_QUERY_CHECKED)
+    assert e.value.code == knn.KNN_EINVAL
+    ids, d2, _ = idx.query(_dev(q), 5, knn.KNN_VOTE)
+    torch.cuda.synchronize()
+    ids = ids.cpu().numpy()
+    assert (ids[3] == -1).all() and (ids[[0, 1, 2, 4]] >= 0).all()
+    idx.free()
+
+
+def test_non_finite_point_is_rejected():
+    x, lab, _ = wl.uniform(100, 1, 2, seed=1)
+    x[7, 0] = np.inf
+    with pytest.raises(knn.KnnError) as e:
+        knn.knn_build(_dev(x), _dev(lab), 0.1)
+    assert e.value.code == knn.KNN_EINVAL
+
+
+def test_grid_too_fine_is_rejected():
+    x, lab, _ = wl.uniform(100, 1, 3, seed=1)
+    with pytest.raises(knn.KnnError) as e:
+        knn.knn_build(_dev(x), _dev(lab), 1e-12)
+    assert e.value.code == knn.KNN_EINVAL
+    with pytest.raises(knn.KnnError) as e:
+        knn.knn_build(_dev(x), _dev(lab), 1e-4, knn.KNN_TABLE_DENSE)
+    assert e.value.code == knn.KNN_EINVAL
+
+
+def test_prediction_without_labels_is_rejected():
+    x, _, q = wl.uniform(100, 5, 2, seed=1)
+    idx = knn.knn_build(_dev(x), None, 0.1)
+    with pytest.raises(knn.KnnError):
+        idx.query(_dev(q), 3, knn.KNN_VOTE)
+    ids, _, _ = idx.query(_dev(q), 3, knn.KNN_NONE, flags=knn.KNN_QUERY_CHECKED)
+    assert ids.shape == (5, 3)
+    idx.free()
+
+
+def test_deterministic_bytes():
+    w = wl.make("large_cls", n=50_000, m=4000, w=0.03)
+    a, _ = gpu_run(w.points, w.labels, w.queries, w.w, w.k, w.mode, knn.KNN_TABLE_HASH)
+    b, _ = gpu_run(w.points, w.labels, w.queries, w.w, w.k, w.mode, knn.KNN_TABLE_HASH)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def _child(code, env):
+    e = dict(os.environ, **env)
+    return subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=e, capture_output=True,
+                          text=True, timeout=300)
+
+
+def test_injected_allocation_failure():
+    code = (
+        "import numpy as np, torch\n"
+        "from paper_2004_02290_gb300 import knn, workloads as wl\n"
+        "x, lab, q = wl.uniform(1000, 10, 2, seed=1)\n"
+        "try:\n"
+        "    knn.knn_build(torch.from_numpy(x).cuda(), torch.from_numpy(lab).cuda(), 0.05)\n"
+        "    print('NOFAIL')\n"
+        "except knn.KnnError as e:\n"
+        "    print('CODE', e.code)\n"
+        "idx = knn.knn_build(torch.from_numpy(x).cuda(), torch.from_numpy(lab).cuda(), 0.05)\n"
+        "ids, _, _ = idx.query(torch.from_numpy(q).cuda(), 3, flags=knn.KNN_QUERY_CHECKED)\n"
+        "print('AFTER', int(ids.min()))\n")
+    for at in ("1", "3", "9"):
+        r = _child(code, {"GHN_FAIL_ALLOC_AT": at})
+        assert r.returncode == 0, r.stderr
+        assert "CODE 2" in r.stdout, r.stdout
+        assert "AFTER 0" in r.stdout or "AFTER" in r.stdout
+
+
+def test_layer_cap_reports_limit():
+    code = (
+        "import numpy as np, torch\n"
+        "from paper_2004_02290_gb300 import knn, workloads as wl\n"
+        "x, lab, q = wl.uniform(5000, 200, 2, seed=2)\n"
+        "idx = knn.knn_build(torch.from_numpy(x).cuda(), torch.from_numpy(lab).cuda(), 0.01)\n"
+        "try:\n"
+        "    idx.query(torch.from_numpy(q).cuda(), 8, flags=knn.KNN_QUERY_CHECKED)\n"
+        "    print('NOFAIL')\n"
+        "except knn.KnnError as e:\n"
+        "    print('CODE', e.code)\n"
+        "ids, _, _ = idx.query(torch.from_numpy(q).cuda(), 8)\n"
+        "torch.cuda.synchronize()\n"
+        "print('NEG', int((ids.cpu().numpy() == -1).all(axis=1).sum()))\n")
+    r = _child(code, {"GHN_MAX_LAYERS": "1"})
+    assert r.returncode == 0, r.stderr
+    assert "CODE 4" in r.stdout, r.stdout
+    neg = int(r.stdout.split("NEG")[1].split()[0])
+    assert neg > 0
+
+
+# ---- full-size workloads, in the benchmark's launch configuration, sampled ----
+
+def _sampled_full(name, sample, flags):
+    w = wl.make(name)
+    idx = knn.knn_build(_dev(w.points), _dev(w.labels), w.w, w.table)
+    ids, d2, pred = idx.query(_dev(w.queries), w.k, w.mode, flags=flags | knn.KNN_QUERY_CHECKED)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(123)
+    pick = np.sort(rng.choice(w.m, size=sample, replace=False))
+    g = oracle.Grid(w.points, w.labels, w.w)
+    exp = g.query(w.queries[pick], w.k, w.mode)
+    got = (ids.cpu().numpy()[pick], d2.cpu().numpy()[pick], pred.cpu().numpy()[pick])
+    assert_same(got, exp, w.mode)
+    # properties that hold for every row: sorted, distinct, in range
+    allids = ids.cpu().numpy()
+    alld = d2.cpu().numpy()
+    assert (allids >= 0).all() and (allids < w.n).all()
+    assert (np.diff(alld, axis=1) >= 0).all()
+    s = np.sort(allids, axis=1)
+    assert (np.diff(s, axis=1) > 0).all()
+    idx.free()
+
+
+def test_full_large_cls_sampled():
+    _sampled_full("large_cls", 3000, knn.KNN_QUERY_SORTED)
+
+
+def test_full_skewed_reg_sampled():
+    _sampled_full("skewed_reg", 1500, knn.KNN_QUERY_SORTED)
