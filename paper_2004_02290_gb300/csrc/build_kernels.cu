@@ -424,6 +424,19 @@ __global__ void hash_insert_kernel(const unsigned long long* __restrict__ cell_k
     }
 }
 
+// Occupancy bitmap: one bit per linear cell id of the box.
+__global__ void bitmap_kernel(const unsigned long long* __restrict__ cell_key,
+                              const GridDev* __restrict__ gdev, unsigned int* __restrict__ bm)
+{
+    const unsigned long long u = gdev->ncells;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < (long long)u;
+         c += stride) {
+        const unsigned long long id = cell_key[c];
+        atomicOr(bm + (id >> 5), 1u << (unsigned)(id & 31ull));
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Gather the point rows into cell order, padded to 2, 4 or 8 floats so that a
 // row is one 8-, 16- or two 16-byte loads in the query kernel.
@@ -642,6 +655,16 @@ cudaError_t launch_hash_table(const unsigned long long* cell_key, const unsigned
                                                                                 cell_start, gdev,
                                                                                 slots);
     count_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bitmap(const unsigned long long* cell_key, const GridDev* gdev,
+                          unsigned int* bitmap, unsigned long long words, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(bitmap, 0, words * sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    bitmap_kernel<<<grid_for((long long)words * 16, 256), 256, 0, s>>>(cell_key, gdev, bitmap);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -32,6 +32,7 @@ struct ghn_index {
     unsigned int* dstart = nullptr;  // dense table
     HashSlot* slots = nullptr;       // hash table
     unsigned long long max_slots = 0;
+    unsigned int* bitmap = nullptr;  // hash: occupancy bit per cell of the box, or null
     GridDev* gdev = nullptr;
     cudaEvent_t last_use = nullptr;
     // filled on first inspection
@@ -73,6 +74,29 @@ long long fail_alloc_at()
         const char* s = getenv("GHN_FAIL_ALLOC_AT");
         return s ? atoll(s) : 0ll;
     }();
+    return v;
+}
+
+// Deferral thresholds of the warp kernel (see query_kernel.cuh); a query
+// with a layer of more rows, or a row batch of more candidates, goes to the
+// cooperative kernel.  GHN_HEAVY_ROWS / GHN_HEAVY_CANDS override them.
+unsigned int env_uint(const char* name, unsigned int dflt)
+{
+    const char* s = getenv(name);
+    if (!s || !*s) return dflt;
+    const long long v = atoll(s);
+    return v <= 0 ? 0xffffffffu : (unsigned int)(v > 0xffffffffll ? 0xffffffffll : v);
+}
+
+unsigned int heavy_rows_env()
+{
+    static unsigned int v = env_uint("GHN_HEAVY_ROWS", 1024u);
+    return v;
+}
+
+unsigned int heavy_cands_env()
+{
+    static unsigned int v = env_uint("GHN_HEAVY_CANDS", 2048u);
     return v;
 }
 
@@ -253,6 +277,7 @@ void free_index(ghn_index* x)
     dfree(x->labels, s);
     dfree(x->dstart, s);
     dfree(x->slots, s);
+    dfree(x->bitmap, s);
     dfree(x->gdev, s);
     if (x->last_use) cudaEventDestroy(x->last_use);
     delete x;
@@ -420,6 +445,15 @@ knn_status build_impl(const float* points_user, const void* labels_user, long lo
                 return fail(st);
             }
             e = launch_hash_table(cell_key, cell_start, x->gdev, x->slots, cap, s);
+            // an occupancy bitmap over the box when it is small next to the
+            // points (at most 64 bytes per point, 1 GiB): a row's occupied
+            // cells then cost one word load, and only two of them are probed
+            if (e == cudaSuccess && space <= (1ull << 33) && space / 8ull <= 64ull * (unsigned long long)n) {
+                const unsigned long long words = (space + 31ull) / 32ull;
+                st = dalloc(&x->bitmap, (size_t)words, s, "occupancy bitmap");
+                if (st != KNN_OK) return fail(st);
+                e = launch_bitmap(cell_key, x->gdev, x->bitmap, words, s);
+            }
         }
         if (e != cudaSuccess) {
             return fail(cuda_fail(e, "cell table"));
@@ -473,11 +507,16 @@ knn_status query_impl(const ghn_index* x, const float* queries_user, long long m
                    (stats_user && stats != stats_user);
 
         g_timer.mark("stage", s);
-        // scratch: work counter and status word
+        // scratch: work counter, status word, deferral counters, deferred list
         unsigned long long* scratch = nullptr;
-        st = tmp.alloc(&scratch, 2, "query scratch");
+        st = tmp.alloc(&scratch, 4, "query scratch");
         if (st != KNN_OK) return st;
-        GHN_CHECK(cudaMemsetAsync(scratch, 0, 2 * sizeof(unsigned long long), s), "memset");
+        GHN_CHECK(cudaMemsetAsync(scratch, 0, 4 * sizeof(unsigned long long), s), "memset");
+        unsigned int* heavy = nullptr;
+        if (!stats) {
+            st = tmp.alloc(&heavy, (size_t)m, "deferred queries");
+            if (st != KNN_OK) return st;
+        }
 
         const unsigned int* order = nullptr;
         if ((flags & KNN_QUERY_SORTED) && m > 1 && x->key_bits > 0) {
@@ -514,9 +553,15 @@ knn_status query_impl(const ghn_index* x, const float* queries_user, long long m
         a.labels = x->labels;
         a.dstart = x->dstart;
         a.slots = x->slots;
+        a.bitmap = x->bitmap;
         a.gdev = x->gdev;
         a.counter = scratch;
         a.status = reinterpret_cast<unsigned int*>(scratch + 1);
+        a.heavy_count = reinterpret_cast<unsigned int*>(scratch + 2);
+        a.heavy_cursor = reinterpret_cast<unsigned int*>(scratch + 2) + 1;
+        a.heavy_list = heavy;
+        a.heavy_rows = heavy_rows_env();
+        a.heavy_cands = heavy_cands_env();
         a.stats = stats;
         a.order = order;
         a.max_layers = max_layers_env();
@@ -594,17 +639,12 @@ void count_launches(long long k) { g_launches += k; }
 
 cudaError_t launch_query(const QueryArgs& a, int sms, cudaStream_t s)
 {
-    // persistent grid: two 256-thread blocks per SM, fewer when m is small
-    long long blocks = (long long)sms * 2;
-    const long long need = (a.m + 7) / 8;
-    if (blocks > need) blocks = need;
-    if (blocks < 1) blocks = 1;
     const int d = a.g.d;
     count_launches(1);
-    if (d <= 2) return launch_query_d12(a, (int)blocks, s);
-    if (d <= 4) return launch_query_d34(a, (int)blocks, s);
-    if (d <= 6) return launch_query_d56(a, (int)blocks, s);
-    return launch_query_d78(a, (int)blocks, s);
+    if (d <= 2) return launch_query_d12(a, sms, s);
+    if (d <= 4) return launch_query_d34(a, sms, s);
+    if (d <= 6) return launch_query_d56(a, sms, s);
+    return launch_query_d78(a, sms, s);
 }
 
 }  // namespace ghn

@@ -98,6 +98,11 @@ cudaError_t launch_hash_table(const unsigned long long* cell_key, const unsigned
                               const GridDev* gdev, HashSlot* slots, unsigned long long max_slots,
                               cudaStream_t s);
 
+// Occupancy bitmap over the box (bit id set when cell id holds a point);
+// `words` 32-bit words, zeroed here.
+cudaError_t launch_bitmap(const unsigned long long* cell_key, const GridDev* gdev,
+                          unsigned int* bitmap, unsigned long long words, cudaStream_t s);
+
 cudaError_t launch_gather(const float* pts, long long n, int d, const unsigned int* order,
                           float* rows, cudaStream_t s);
 
@@ -116,9 +121,15 @@ struct QueryArgs {
     const unsigned int* labels;     // n raw 32-bit outputs, training order, or null
     const unsigned int* dstart;     // dense: ncell_space + 1 row offsets
     const HashSlot* slots;          // hash table
+    const unsigned int* bitmap;     // hash: one bit per cell of the box, or null
     const GridDev* gdev;
     unsigned long long* counter;    // work counter, zero at launch
     unsigned int* status;           // status bits
+    unsigned int* heavy_list;       // deferred queries (m entries), or null: no deferral
+    unsigned int* heavy_count;      // deferred queries so far, zero at launch
+    unsigned int* heavy_cursor;     // cooperative kernel's work counter, zero at launch
+    unsigned int heavy_rows;        // defer a query whose layer has more rows than this
+    unsigned int heavy_cands;       // or whose row batch holds more candidates than this
     long long* stats;               // m*3 or null (exhaustive counting walk)
     const unsigned int* order;      // visiting order of queries or null
     long long max_layers;           // 0 = no cap
@@ -127,10 +138,11 @@ struct QueryArgs {
 
 cudaError_t launch_query(const QueryArgs& a, int num_sms, cudaStream_t s);
 
-cudaError_t launch_query_d12(const QueryArgs& a, int blocks, cudaStream_t s);
-cudaError_t launch_query_d34(const QueryArgs& a, int blocks, cudaStream_t s);
-cudaError_t launch_query_d56(const QueryArgs& a, int blocks, cudaStream_t s);
-cudaError_t launch_query_d78(const QueryArgs& a, int blocks, cudaStream_t s);
+// Persistent launch: as many blocks as fit on `sms` SMs (fewer when m is small).
+cudaError_t launch_query_d12(const QueryArgs& a, int sms, cudaStream_t s);
+cudaError_t launch_query_d34(const QueryArgs& a, int sms, cudaStream_t s);
+cudaError_t launch_query_d56(const QueryArgs& a, int sms, cudaStream_t s);
+cudaError_t launch_query_d78(const QueryArgs& a, int sms, cudaStream_t s);
 
 // Query keys for the locality order (cell id of each query, clamped into the box).
 cudaError_t launch_query_keys(const float* q, long long m, const GridConst& g,

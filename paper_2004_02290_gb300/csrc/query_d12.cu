@@ -4,11 +4,11 @@
 
 namespace ghn {
 
-cudaError_t launch_query_d12(const QueryArgs& a, int blocks, cudaStream_t s)
+cudaError_t launch_query_d12(const QueryArgs& a, int sms, cudaStream_t s)
 {
     switch (a.g.d) {
-    case 1: return qk::launch_d<1>(a, blocks, s);
-    case 2: return qk::launch_d<2>(a, blocks, s);
+    case 1: return qk::launch_d<1>(a, sms, s);
+    case 2: return qk::launch_d<2>(a, sms, s);
     default: return cudaErrorInvalidValue;
     }
 }

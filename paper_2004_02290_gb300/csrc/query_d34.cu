@@ -4,11 +4,11 @@
 
 namespace ghn {
 
-cudaError_t launch_query_d34(const QueryArgs& a, int blocks, cudaStream_t s)
+cudaError_t launch_query_d34(const QueryArgs& a, int sms, cudaStream_t s)
 {
     switch (a.g.d) {
-    case 3: return qk::launch_d<3>(a, blocks, s);
-    case 4: return qk::launch_d<4>(a, blocks, s);
+    case 3: return qk::launch_d<3>(a, sms, s);
+    case 4: return qk::launch_d<4>(a, sms, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -4,11 +4,11 @@
 
 namespace ghn {
 
-cudaError_t launch_query_d56(const QueryArgs& a, int blocks, cudaStream_t s)
+cudaError_t launch_query_d56(const QueryArgs& a, int sms, cudaStream_t s)
 {
     switch (a.g.d) {
-    case 5: return qk::launch_d<5>(a, blocks, s);
-    case 6: return qk::launch_d<6>(a, blocks, s);
+    case 5: return qk::launch_d<5>(a, sms, s);
+    case 6: return qk::launch_d<6>(a, sms, s);
     default: return cudaErrorInvalidValue;
     }
 }

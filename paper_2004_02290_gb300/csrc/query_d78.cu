@@ -4,11 +4,11 @@
 
 namespace ghn {
 
-cudaError_t launch_query_d78(const QueryArgs& a, int blocks, cudaStream_t s)
+cudaError_t launch_query_d78(const QueryArgs& a, int sms, cudaStream_t s)
 {
     switch (a.g.d) {
-    case 7: return qk::launch_d<7>(a, blocks, s);
-    case 8: return qk::launch_d<8>(a, blocks, s);
+    case 7: return qk::launch_d<7>(a, sms, s);
+    case 8: return qk::launch_d<8>(a, sms, s);
     default: return cudaErrorInvalidValue;
     }
 }

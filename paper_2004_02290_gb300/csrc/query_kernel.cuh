@@ -1,32 +1,40 @@
 // Query kernel: exploration (Sec. III.B, Algorithm 2) and prediction (Sec. I).
 //
 // One warp per query, persistent grid, queries taken from a global counter.
-// For layer L = 0, 1, 2, ... the warp enumerates the rows of cube(L) clipped to
-// the box of occupied cells.  A row is a run of cells along the last dimension
-// with fixed outer coordinates; the cells of one row have consecutive linear
-// ids, so their points are one contiguous range of the cell-ordered rows.
-// Rows whose outer coordinates are at Chebyshev distance L from the central
-// cell lie entirely on layer L; other rows touch layer L only in their two end
-// cells.  Each lane resolves one row into at most two row ranges; the warp
-// flattens the ranges of 32 rows and streams their points 32 at a time with
-// coalesced 8/16/32-byte loads.
 //
-// The k-buffer ("a heap of size k", Sec. III.B) is a sorted list of 64-bit
-// keys (squared-distance bits << 32 | training index) spread over the lanes
-// (one key per lane for k <= 32, two for k <= 64).  Squared distances are
-// non-negative floats, so unsigned comparison of the keys is the order
-// (distance, index).  A candidate enters by a ballot-and-shift insertion.
-// "Update" (the stop test of Sec. III.B) is: some point of the layer entered
-// the buffer; it depends only on which points the layer holds, not on the
-// order they are offered in, so the warp-parallel walk stops exactly where a
-// sequential walk does.
+// Layers.  For L = 0, 1, 2, ... the warp enumerates the rows of cube(L)
+// clipped to the box of occupied cells.  A row is the run of cells along the
+// last dimension with fixed outer coordinates.  Cells of one row have
+// consecutive linear ids, so the points of any run of occupied cells of a row
+// are one contiguous range of the cell-ordered rows.  A row whose outer
+// coordinates are at Chebyshev distance L from the central cell lies wholly on
+// layer L; any other row meets layer L only in its two end cells.  So a lane
+// turns one row into at most two ranges, with at most two table lookups per
+// range: the dense table gives a range directly; with the hash table an
+// occupancy bitmap (when the box is small enough to afford one) finds the
+// first and last occupied cell of the run, and only those two are probed.
 //
-// Geometric skipping (result-preserving): once the buffer is full, a row, or a
-// whole layer, whose distance from the query provably exceeds the k-th
-// distance cannot contribute an update and is not read.  The bound works in
-// cell units with a relative margin far larger than the rounding of Eq. 1 and
-// of the distance, so no point that could enter the buffer is ever skipped.
-// knn_query_stats runs the same walk without skipping and counts the work.
+// Candidates.  The warp flattens the ranges of 32 rows and streams their
+// points with coalesced 8/16/32-byte loads, several chunks of 32 in flight.
+//
+// k-buffer ("a heap of size k", Sec. III.B).  Sorted 64-bit keys (squared
+// distance bits << 32 | training index) over the lanes, one key per lane for
+// k <= 32 and two for k <= 64.  Squared distances are non-negative floats, so
+// unsigned order of the keys is the order (distance, index).  Few entering
+// candidates are inserted one by one (ballot and shift); many are sorted
+// (bitonic) and merged.  "Update" (the stop test of Sec. III.B) is: some point
+// of the layer entered the buffer.  That depends only on which points the
+// layer holds, not on the order in which they are offered, so the parallel
+// walk stops exactly where a sequential walk does.
+//
+// Skipping (result-preserving).  Once the buffer is full, the k-th distance r
+// bounds the search: each axis of the cube is clipped to the cells within r of
+// the query, rows whose outer coordinates are farther than r are dropped, and
+// a layer with no cell left within r ends the walk (it cannot update).  The
+// bounds work in cell units with a margin (1e-6 relative per axis, 1e-5 on the
+// square) far above the rounding of Eq. 1 and of the distance, so no point
+// that could enter the buffer is skipped.  knn_query_stats runs the same walk
+// without skipping and counts the method's work.
 
 #pragma once
 
@@ -100,6 +108,20 @@ struct TopK {
         kth = kEmptyKey;
     }
 
+    __device__ __forceinline__ void refresh_kth()
+    {
+        const int e = k - 1;
+        if (count < k) {
+            kth = kEmptyKey;
+        } else if constexpr (NS == 1) {
+            kth = __shfl_sync(FULL, s[0], e & 31);
+        } else {
+            const unsigned long long a = __shfl_sync(FULL, s[0], e & 31);
+            const unsigned long long b = __shfl_sync(FULL, s[1], e & 31);
+            kth = e < 32 ? a : b;
+        }
+    }
+
     // Insert x (warp-uniform, x < kth).
     __device__ __forceinline__ void insert(unsigned long long x, int lane)
     {
@@ -115,240 +137,536 @@ struct TopK {
             const unsigned long long upa = __shfl_up_sync(FULL, s[0], 1);
             const unsigned long long upb = __shfl_up_sync(FULL, s[1], 1);
             const unsigned long long carry = __shfl_sync(FULL, s[0], 31);
-            // slot 1 (entries 32..63)
-            const int e1 = 32 + lane;
+            const int e1 = 32 + lane;  // slot 1 holds entries 32..63
             if (e1 > pos) s[1] = lane == 0 ? carry : upb;
             if (e1 == pos) s[1] = x;
             if (e1 >= k) s[1] = kEmptyKey;
-            // slot 0 (entries 0..31)
             if (lane > pos) s[0] = upa;
             if (lane == pos) s[0] = x;
             if (lane >= k) s[0] = kEmptyKey;
         }
         if (count < k) ++count;
-        if (count == k) {
-            const int e = k - 1;
-            if constexpr (NS == 1) {
-                kth = __shfl_sync(FULL, s[0], e & 31);
-            } else {
-                const unsigned long long a = __shfl_sync(FULL, s[0], e & 31);
-                const unsigned long long b = __shfl_sync(FULL, s[1], e & 31);
-                kth = e < 32 ? a : b;
+        refresh_kth();
+    }
+
+    // Merge a warp of candidate keys (one per lane, kEmptyKey for none), k <= 32.
+    __device__ __forceinline__ void merge32(unsigned long long x, int lane)
+    {
+        // bitonic sort of the candidates, ascending with the lane
+#pragma unroll
+        for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                const unsigned long long y = __shfl_xor_sync(FULL, x, stride);
+                const bool up = (lane & size) == 0 || size == 32;
+                const bool lower = (lane & stride) == 0;
+                x = (lower == up) ? (x < y ? x : y) : (x < y ? y : x);
             }
+        }
+        // the lane-wise min of the buffer and the reversed candidates holds the
+        // 32 smallest of both, as a bitonic sequence; one bitonic merge sorts it
+        const unsigned long long rev = __shfl_sync(FULL, x, 31 - lane);
+        unsigned long long c = s[0] < rev ? s[0] : rev;
+#pragma unroll
+        for (int stride = 16; stride > 0; stride >>= 1) {
+            const unsigned long long y = __shfl_xor_sync(FULL, c, stride);
+            c = ((lane & stride) == 0) ? (c < y ? c : y) : (c < y ? y : c);
+        }
+        s[0] = lane < k ? c : kEmptyKey;
+        count = __popc(__ballot_sync(FULL, s[0] != kEmptyKey));
+        refresh_kth();
+    }
+};
+
+// Margin for the rounding of Eq. 1 and of float conversions (cell units).
+__device__ __forceinline__ float axis_margin(float c, float u)
+{
+    return 1e-6f * (fabsf(c) + fabsf(u) + 2.0f);
+}
+
+// Squared lower bound of the distance along one axis between a query at u and
+// any point of the cells [c0, c1] of that axis (cell c spans [c, c + 1) in the
+// quotient of Eq. 1): the gap in cell units less the margin, scaled by w
+// before squaring so that the bound overflows only where every distance does.
+__device__ __forceinline__ float axis_gap2(long long c0, long long c1, float u, float w)
+{
+    const float lo = (float)c0, hi = (float)(c1 + 1);
+    const float g = fmaxf(0.0f, fmaxf(lo - u, u - hi) - axis_margin(fabsf(lo) + fabsf(hi), u));
+    const float gw = g * w;
+    return gw * gw;
+}
+
+// Bits [b0, b1] of the occupancy bitmap: first and last set bit (b1 + 1 if none).
+__device__ __forceinline__ void bitmap_span(const unsigned int* bm, unsigned long long b0,
+                                            unsigned long long b1, unsigned long long& first,
+                                            unsigned long long& last, int& count, bool want_count)
+{
+    first = b1 + 1ull;
+    last = b1 + 1ull;
+    count = 0;
+    const unsigned long long w0 = b0 >> 5, w1 = b1 >> 5;
+    for (unsigned long long wi = w0; wi <= w1; ++wi) {
+        unsigned int word = __ldg(bm + wi);
+        if (wi == w0) word &= 0xffffffffu << (b0 & 31ull);
+        if (wi == w1) word &= 0xffffffffu >> (31ull - (b1 & 31ull));
+        if (word) {
+            if (first > b1) first = (wi << 5) + (unsigned long long)(__ffs(word) - 1);
+            last = (wi << 5) + (unsigned long long)(31 - __clz(word));
+            if (want_count) count += __popc(word);
+        }
+    }
+}
+
+// Probe the open-addressing table for cell id `key`: its row range, or 0/0.
+__device__ __forceinline__ void hash_lookup(const HashSlot* slots, unsigned long long hmask,
+                                            unsigned long long key, unsigned int& st,
+                                            unsigned int& en, bool& found)
+{
+    unsigned long long h = mix64(key) & hmask;
+    st = 0u;
+    en = 0u;
+    found = false;
+    for (unsigned long long probe = 0; probe <= hmask; ++probe) {
+        const ulonglong2 e = __ldg(reinterpret_cast<const ulonglong2*>(slots) + h);
+        if (e.x == key) {
+            st = (unsigned int)e.y;
+            en = (unsigned int)(e.y >> 32);
+            found = true;
+            return;
+        }
+        if (e.x == kEmptyKey) return;
+        h = (h + 1ull) & hmask;
+    }
+}
+
+// Row range of the occupied cells among the cells [base + x0, base + x1] of one
+// row; `cells` counts the occupied cells (only when counting).
+template <bool DENSE>
+__device__ __forceinline__ void resolve_run(const QueryArgs& a, unsigned long long hmask,
+                                            unsigned long long base, long long x0, long long x1,
+                                            bool counting, unsigned int& st, unsigned int& len,
+                                            long long& cells)
+{
+    st = 0u;
+    len = 0u;
+    const unsigned long long i0 = base + (unsigned long long)x0;
+    const unsigned long long i1 = base + (unsigned long long)x1;
+    if constexpr (DENSE) {
+        const unsigned int s0 = __ldg(a.dstart + i0);
+        const unsigned int e0 = __ldg(a.dstart + i1 + 1ull);
+        if (counting) {
+            unsigned int prev = s0;
+            for (unsigned long long i = i0; i <= i1; ++i) {
+                const unsigned int nx = __ldg(a.dstart + i + 1ull);
+                cells += nx > prev;
+                prev = nx;
+            }
+        }
+        st = s0;
+        len = e0 - s0;
+    } else if (a.bitmap) {
+        unsigned long long f, l;
+        int cnt;
+        bitmap_span(a.bitmap, i0, i1, f, l, cnt, counting);
+        cells += cnt;
+        if (f > i1) return;
+        unsigned int s0, e0, s1, e1;
+        bool ok0, ok1;
+        hash_lookup(a.slots, hmask, f, s0, e0, ok0);
+        if (l == f) {
+            s1 = s0;
+            e1 = e0;
+            ok1 = ok0;
+        } else {
+            hash_lookup(a.slots, hmask, l, s1, e1, ok1);
+        }
+        if (ok0 && ok1) {
+            st = s0;
+            len = e1 - s0;
+        }
+    } else {
+        unsigned int s0 = 0xffffffffu, e0 = 0u;
+        for (unsigned long long i = i0; i <= i1; ++i) {
+            unsigned int cs, ce;
+            bool ok;
+            hash_lookup(a.slots, hmask, i, cs, ce, ok);
+            if (ok) {
+                s0 = cs < s0 ? cs : s0;
+                e0 = ce > e0 ? ce : e0;
+                ++cells;
+            }
+        }
+        if (e0 > 0u) {
+            st = s0;
+            len = e0 - s0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Per-query pieces shared by the warp kernel and the cooperative kernel
+// ---------------------------------------------------------------------------
+
+template <int D>
+struct Query {
+    float q[D];
+    float u[D];       // Eq. 1 quotient (q - o) / w, single precision
+    long long c0[D];  // central cell, clamped to [-2^40, 2^40]
+    long long lmin;   // first layer that reaches the box of occupied cells
+    bool finite;
+};
+
+template <int D>
+__device__ __forceinline__ void query_setup(const QueryArgs& a, long long qid, Query<D>& s)
+{
+    s.finite = true;
+    s.lmin = 0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        s.q[j] = __ldg(a.q + qid * D + j);
+        s.finite &= isfinite(s.q[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        // Eq. 1 on the query, single precision, round to nearest
+        s.u[j] = __fdiv_rn(__fsub_rn(s.q[j], a.g.lo[j]), a.g.w);
+        float f = floorf(s.u[j]);
+        f = fminf(fmaxf(f, -kQueryClamp), kQueryClamp);  // NaN becomes -2^40
+        s.c0[j] = (long long)f;
+        long long gap = 0;
+        if (s.c0[j] < 0) gap = -s.c0[j];
+        if (s.c0[j] > a.g.cmax[j]) gap = s.c0[j] - a.g.cmax[j];
+        s.lmin = gap > s.lmin ? gap : s.lmin;
+    }
+}
+
+// cube(L) clipped to the box; when skipping, also clipped to the cells within
+// the k-th distance kd of the query.  `empty`: no cell of layer L is left.
+template <int D>
+struct Layer {
+    int lo[D], hi[D];  // every clipped coordinate fits 32 bits
+    bool covers;       // cube(L) covers the whole box
+    bool empty;
+};
+
+template <int D>
+__device__ __forceinline__ void layer_box(const QueryArgs& a, const Query<D>& s, long long L,
+                                          bool skipping, float kd, Layer<D>& b)
+{
+    b.covers = true;
+    b.empty = false;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        b.lo[j] = (int)(s.c0[j] - L < 0 ? 0 : s.c0[j] - L);
+        b.hi[j] = (int)(s.c0[j] + L > a.g.cmax[j] ? a.g.cmax[j] : s.c0[j] + L);
+        b.covers &= (s.c0[j] - L <= 0) && (s.c0[j] + L >= a.g.cmax[j]);
+    }
+    if (!skipping) return;
+    // a cell farther than kd along one axis cannot hold a point that enters
+    const float r = __fdiv_rn(sqrtf(kd), a.g.w) * (1.0f + 2e-5f);
+    bool shell = false;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const float m = 1e-6f * (fabsf(s.u[j]) + r) + 1e-3f;
+        const long long a0 = (long long)fminf(fmaxf(floorf(s.u[j] - r - m), -4e18f), 4e18f);
+        const long long a1 = (long long)fminf(fmaxf(floorf(s.u[j] + r + m), -4e18f), 4e18f);
+        if (a0 > b.lo[j]) b.lo[j] = a0 > b.hi[j] ? b.hi[j] + 1 : (int)a0;
+        if (a1 < b.hi[j]) b.hi[j] = a1 < b.lo[j] ? b.lo[j] - 1 : (int)a1;
+        b.empty |= b.lo[j] > b.hi[j];
+        shell |= (s.c0[j] - L >= b.lo[j] && s.c0[j] - L <= b.hi[j]) ||
+                 (s.c0[j] + L >= b.lo[j] && s.c0[j] + L <= b.hi[j]);
+    }
+    b.empty |= !shell;
+}
+
+template <int D>
+__device__ __forceinline__ unsigned long long layer_rows(const Layer<D>& b)
+{
+    unsigned long long nrows = 1ull;
+#pragma unroll
+    for (int j = 0; j < D - 1; ++j) nrows *= (unsigned long long)(b.hi[j] - b.lo[j] + 1);
+    return nrows;
+}
+
+// Row odometer over the outer axes 0..D-2 of the layer box, last outer axis
+// fastest: digits of the starting row and of the stride between visits.
+template <int D>
+struct RowWalk {
+    int dig[D > 1 ? D - 1 : 1];
+    int inc[D > 1 ? D - 1 : 1];
+
+    __device__ __forceinline__ void start(const Layer<D>& b, unsigned int first, unsigned int step)
+    {
+#pragma unroll
+        for (int j = D - 2; j >= 0; --j) {
+            const unsigned int e = (unsigned int)(b.hi[j] - b.lo[j] + 1);
+            dig[j] = (int)(first % e);
+            first /= e;
+            inc[j] = (int)(step % e);
+            step /= e;
+        }
+    }
+    __device__ __forceinline__ void advance(const Layer<D>& b)
+    {
+        int carry = 0;
+#pragma unroll
+        for (int j = D - 2; j >= 0; --j) {
+            const int e = b.hi[j] - b.lo[j] + 1;
+            const int v = dig[j] + inc[j] + carry;
+            carry = v >= e;
+            dig[j] = carry ? v - e : v;
         }
     }
 };
 
-// Lower bound, in cell units, of |v - u| over v in the cells [a, b] of one
-// dimension (v = (p - o) / w as Eq. 1 computes it for points of those cells).
-__device__ __forceinline__ float axis_gap(long long a, long long b, float u)
+// The ranges of one row of layer L: the whole clipped row when its outer
+// coordinates are on the shell, else its two end cells.  A run that the
+// k-th distance kth_d excludes is dropped when `prune` is set.
+template <int D, bool DENSE>
+__device__ __forceinline__ void row_ranges(const QueryArgs& a, unsigned long long hmask,
+                                           const Query<D>& s, const Layer<D>& b,
+                                           const RowWalk<D>& rw, long long L, bool prune,
+                                           float kth_d, bool counting, unsigned int& sa,
+                                           unsigned int& la, unsigned int& sb, unsigned int& lb,
+                                           long long& cells)
 {
-    const float lo = (float)a, hi = (float)(b + 1);
-    return fmaxf(0.0f, fmaxf(lo - u, u - hi));
+    constexpr int dl = D - 1;
+    long long ocheb = 0;
+    unsigned long long base = 0ull;
+    float og2 = 0.0f;
+#pragma unroll
+    for (int j = 0; j < D - 1; ++j) {
+        const long long c = (long long)(b.lo[j] + rw.dig[j]);
+        const long long dd = c > s.c0[j] ? c - s.c0[j] : s.c0[j] - c;
+        ocheb = dd > ocheb ? dd : ocheb;
+        base += (unsigned long long)c * a.g.stride[j];
+        og2 += axis_gap2(c, c, s.u[j], a.g.w);
+    }
+    long long x0a, x1a, x0b, x1b;
+    if (ocheb == L) {
+        x0a = b.lo[dl];
+        x1a = b.hi[dl];
+        x0b = 1;
+        x1b = 0;
+    } else {
+        x0a = x1a = s.c0[dl] - L;
+        x0b = x1b = s.c0[dl] + L;
+        if (x0a < b.lo[dl] || x0a > b.hi[dl]) {
+            x0a = 1;
+            x1a = 0;
+        }
+        if (x0b < b.lo[dl] || x0b > b.hi[dl]) {
+            x0b = 1;
+            x1b = 0;
+        }
+    }
+    sa = la = sb = lb = 0u;
+    if (x0a <= x1a &&
+        !(prune && (og2 + axis_gap2(x0a, x1a, s.u[dl], a.g.w)) * (1.0f - 1e-5f) > kth_d))
+        resolve_run<DENSE>(a, hmask, base, x0a, x1a, counting, sa, la, cells);
+    if (x0b <= x1b &&
+        !(prune && (og2 + axis_gap2(x0b, x1b, s.u[dl], a.g.w)) * (1.0f - 1e-5f) > kth_d))
+        resolve_run<DENSE>(a, hmask, base, x0b, x1b, counting, sb, lb, cells);
+    if (la == 0u) {
+        sa = sb;
+        la = lb;
+        lb = 0u;
+    }
 }
 
-// Margin for the rounding of Eq. 1 and of the float conversions (cell units).
-__device__ __forceinline__ float axis_margin(long long c, float u)
-{
-    return 1e-6f * (fabsf((float)c) + fabsf(u) + 2.0f);
-}
-
-template <int D, int NS, bool DENSE>
-__global__ void __launch_bounds__(kThreads, 2) query_kernel(const QueryArgs a)
+// Key (squared distance bits << 32 | training index) of the stored row `pos`,
+// or kEmptyKey when it cannot beat the k-th key (open: the buffer is not full).
+template <int D>
+__device__ __forceinline__ unsigned long long candidate_key(const QueryArgs& a, const Query<D>& s,
+                                                            unsigned int pos, bool open,
+                                                            float kth_d)
 {
     constexpr int P = row_floats(D);
-    __shared__ unsigned int s_end[kWarps][32];   // inclusive end of each lane's ranges
-    __shared__ unsigned int s_beg[kWarps][32];   // exclusive start of each lane's ranges
-    __shared__ unsigned int s_a[kWarps][32];     // first range: start
-    __shared__ unsigned int s_la[kWarps][32];    // first range: length
-    __shared__ unsigned int s_b[kWarps][32];     // second range: start
+    Row<P> row;
+    row.load(a.rows, pos);
+    const unsigned int rid = __ldg(a.rid + pos);
+    float acc = 0.0f;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const float dj = __fsub_rn(s.q[j], row.v[j]);
+        acc = __fadd_rn(acc, __fmul_rn(dj, dj));
+    }
+    if (!(open || acc <= kth_d)) return kEmptyKey;
+    return ((unsigned long long)__float_as_uint(acc) << 32) | rid;
+}
+
+// Offer one key per lane to the buffer; true when some key entered it.  Keys
+// not below `cap` are refused (the cooperative kernel's block-wide k-th key).
+template <int NS>
+__device__ __forceinline__ bool offer(TopK<NS>& tk, unsigned long long key, int lane,
+                                      unsigned long long cap = kEmptyKey)
+{
+    const bool pass = key < (tk.kth < cap ? tk.kth : cap);
+    unsigned int pm = __ballot_sync(FULL, pass);
+    if (pm == 0u) return false;
+    if (NS == 1 && __popc(pm) > 6) {
+        tk.merge32(pass ? key : kEmptyKey, lane);
+    } else {
+        while (pm) {
+            const int src = __ffs(pm) - 1;
+            pm &= pm - 1u;
+            const unsigned long long x = __shfl_sync(FULL, key, src);
+            if (x < tk.kth) tk.insert(x, lane);  // x < cap already
+        }
+    }
+    return true;
+}
+
+// ids, squared distances and the prediction of one query, from its buffer.
+template <int NS>
+__device__ __forceinline__ void write_outputs(const QueryArgs& a, long long qid,
+                                              const TopK<NS>& tk, bool limited, int lane)
+{
+    const long long obase = qid * (long long)a.k;
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+        const int e = i * 32 + lane;
+        if (e < a.k) {
+            const unsigned long long key = limited ? kEmptyKey : tk.s[i];
+            const bool ok = key != kEmptyKey;
+            a.ids[obase + e] = ok ? (int)(unsigned int)key : -1;
+            if (a.dist2)
+                a.dist2[obase + e] = ok ? __uint_as_float((unsigned)(key >> 32)) : INFINITY;
+        }
+    }
+    const int found = limited ? 0 : tk.count;
+    if (a.mode == 0 && a.pred) {
+        // majority label among the found neighbours, ties to the smallest label
+        unsigned int lab[NS];
+        bool val[NS];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            val[i] = i * 32 + lane < found;
+            lab[i] = val[i] ? __ldg(a.labels + (unsigned int)tk.s[i]) : 0u;
+        }
+        unsigned long long best = 0ull;
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            int cnt = 0;
+            for (int e = 0; e < found; ++e) {
+                unsigned int other;
+                if constexpr (NS == 1) {
+                    other = __shfl_sync(FULL, lab[0], e);
+                } else {
+                    const unsigned int o0 = __shfl_sync(FULL, lab[0], e & 31);
+                    const unsigned int o1 = __shfl_sync(FULL, lab[1], e & 31);
+                    other = e < 32 ? o0 : o1;
+                }
+                cnt += other == lab[i];
+            }
+            if (val[i]) {
+                const unsigned long long sc = ((unsigned long long)cnt << 32) |
+                                              (0xffffffffu - (lab[i] ^ 0x80000000u));
+                best = sc > best ? sc : best;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long y = __shfl_xor_sync(FULL, best, o);
+            best = y > best ? y : best;
+        }
+        if (lane == 0)
+            static_cast<int*>(a.pred)[qid] =
+                found ? (int)((0xffffffffu - (unsigned int)best) ^ 0x80000000u) : 0;
+    } else if (a.mode == 1 && a.pred) {
+        // mean of the found neighbours' outputs: double sum in neighbour order
+        float y[NS];
+#pragma unroll
+        for (int i = 0; i < NS; ++i)
+            y[i] = i * 32 + lane < found ? __uint_as_float(__ldg(a.labels + (unsigned int)tk.s[i]))
+                                         : 0.0f;
+        double sum = 0.0;
+        for (int e = 0; e < found; ++e) {
+            float v;
+            if constexpr (NS == 1) {
+                v = __shfl_sync(FULL, y[0], e);
+            } else {
+                const float v0 = __shfl_sync(FULL, y[0], e & 31);
+                const float v1 = __shfl_sync(FULL, y[1], e & 31);
+                v = e < 32 ? v0 : v1;
+            }
+            sum = __dadd_rn(sum, (double)v);
+        }
+        if (lane == 0)
+            static_cast<float*>(a.pred)[qid] =
+                found ? __double2float_rn(__ddiv_rn(sum, (double)found))
+                      : __int_as_float(0x7fc00000);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The warp kernel: one warp per query
+// ---------------------------------------------------------------------------
+
+template <int D, int NS, bool DENSE>
+__global__ void __launch_bounds__(kThreads, (D <= 4 && NS == 1) ? 3 : 2)
+    query_kernel(const QueryArgs a)
+{
+    __shared__ unsigned int s_end[kWarps][32];  // inclusive end of each lane's ranges
+    __shared__ unsigned int s_beg[kWarps][32];  // exclusive start of each lane's ranges
+    __shared__ unsigned int s_a[kWarps][32];    // first range: start
+    __shared__ unsigned int s_la[kWarps][32];   // first range: length
+    __shared__ unsigned int s_b[kWarps][32];    // second range: start
 
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const bool counting = a.stats != nullptr;
-    const float w = a.g.w;
-    const float w2 = __fmul_rn(w, w);
+    const bool may_defer = !counting && a.heavy_list != nullptr;
     unsigned long long hmask = 0ull;
     if constexpr (!DENSE) hmask = a.gdev->hmask;
 
-    for (;;) {
-        unsigned long long qi = 0ull;
-        if (lane == 0) qi = atomicAdd(a.counter, 1ull);
-        qi = __shfl_sync(FULL, qi, 0);
-        if (qi >= (unsigned long long)a.m) break;
+    // the next query is claimed one query ahead, so the atomic's latency
+    // overlaps the current query's work
+    unsigned long long next = 0ull;
+    if (lane == 0) next = atomicAdd(a.counter, 1ull);
+    next = __shfl_sync(FULL, next, 0);
+    while (next < (unsigned long long)a.m) {
+        const unsigned long long qi = next;
+        if (lane == 0) next = atomicAdd(a.counter, 1ull);
         const long long qid = a.order ? (long long)a.order[qi] : (long long)qi;
 
-        float q[D], u[D];
-        long long c0[D];
-        bool finite = true;
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
-            q[j] = __ldg(a.q + qid * D + j);
-            finite &= isfinite(q[j]);
-        }
+        Query<D> s;
+        query_setup(a, qid, s);
         TopK<NS> tk;
         tk.init(a.k);
-        long long L = 0, lmin = 0;
+        long long L = s.lmin;
         long long cells = 0, cands = 0;
-        bool limited = false;
-        if (!finite) {
-            if (lane == 0) atomicOr(a.status, kStatusNonFinite);
-            limited = true;
-        } else {
-#pragma unroll
-            for (int j = 0; j < D; ++j) {
-                // Eq. 1 on the query, single precision, round to nearest
-                u[j] = __fdiv_rn(__fsub_rn(q[j], a.g.lo[j]), w);
-                float f = floorf(u[j]);
-                f = fminf(fmaxf(f, -kQueryClamp), kQueryClamp);
-                c0[j] = (long long)f;
-                long long gap = 0;
-                if (c0[j] < 0) gap = -c0[j];
-                if (c0[j] > a.g.cmax[j]) gap = c0[j] - a.g.cmax[j];
-                lmin = gap > lmin ? gap : lmin;
-            }
-            // layers nearer than the box of occupied cells are empty
-            L = lmin;
-        }
+        bool limited = !s.finite, deferred = false;
+        if (!s.finite && lane == 0) atomicOr(a.status, kStatusNonFinite);
 
         while (!limited) {
-            long long lo[D], hi[D];
-            bool covers = true;
-#pragma unroll
-            for (int j = 0; j < D; ++j) {
-                lo[j] = c0[j] - L < 0 ? 0 : c0[j] - L;
-                hi[j] = c0[j] + L > a.g.cmax[j] ? a.g.cmax[j] : c0[j] + L;
-                covers &= (c0[j] - L <= 0) && (c0[j] + L >= a.g.cmax[j]);
-            }
-            const bool full = tk.count == tk.k;
-            const float kth_d = __uint_as_float((unsigned)(tk.kth >> 32));
-            const bool may_skip = !counting && full && kth_d < 1e30f;
+            Layer<D> b;
+            const float kd0 = __uint_as_float((unsigned)(tk.kth >> 32));
+            layer_box(a, s, L, !counting && tk.count == tk.k && kd0 < 1e30f, kd0, b);
             bool updated = false;
-
-            bool skip_layer = false;
-            if (may_skip && L > 0) {
-                // every cell of layer L is outside cube(L-1): bound the distance
-                // from the query to the sides of that cube that have cells
-                float gmin = INFINITY;
-#pragma unroll
-                for (int j = 0; j < D; ++j) {
-                    const float mj = axis_margin(c0[j] + L, u[j]);
-                    if (c0[j] + L <= a.g.cmax[j])
-                        gmin = fminf(gmin, fmaxf(0.0f, (float)(c0[j] + L) - u[j] - mj));
-                    if (c0[j] - L >= 0)
-                        gmin = fminf(gmin, fmaxf(0.0f, u[j] - (float)(c0[j] - L + 1) - mj));
-                }
-                const float lb = __fmul_rn(__fmul_rn(gmin, gmin), w2) * (1.0f - 1e-5f);
-                skip_layer = lb > kth_d;
-            }
-
-            if (!skip_layer) {
-                // rows of cube(L) clipped to the box: outer dimensions 0..D-2
-                unsigned long long nrows = 1ull;
-#pragma unroll
-                for (int j = 0; j < D - 1; ++j) nrows *= (unsigned long long)(hi[j] - lo[j] + 1);
+            if (!b.empty) {
+                const unsigned long long nrows = layer_rows(b);
                 if (nrows >= (1ull << 32)) {
                     limited = true;
                     if (lane == 0) atomicOr(a.status, kStatusLimit);
                     break;
                 }
-                for (unsigned int rbase = 0; rbase < (unsigned int)nrows; rbase += 32) {
-                    const unsigned int r = rbase + lane;
-                    unsigned int sa = 0, la = 0, sb = 0, lb_ = 0;
-                    if (r < (unsigned int)nrows) {
-                        // decode the row's outer coordinates (last outer dim fastest)
-                        unsigned int rr = r;
-                        long long oc[D > 1 ? D - 1 : 1];
-                        long long ocheb = 0;
-                        unsigned long long base = 0ull;
-                        float og2 = 0.0f;  // squared outer gap (cell units)
-#pragma unroll
-                        for (int j = D - 2; j >= 0; --j) {
-                            const unsigned int ext = (unsigned int)(hi[j] - lo[j] + 1);
-                            oc[j] = lo[j] + (long long)(rr % ext);
-                            rr /= ext;
-                            const long long dd = oc[j] > c0[j] ? oc[j] - c0[j] : c0[j] - oc[j];
-                            ocheb = dd > ocheb ? dd : ocheb;
-                            base += (unsigned long long)oc[j] * a.g.stride[j];
-                            const float gj = fmaxf(0.0f, axis_gap(oc[j], oc[j], u[j]) -
-                                                             axis_margin(oc[j], u[j]));
-                            og2 += gj * gj;
-                        }
-                        // the row's cells on layer L, as up to two runs [x0, x1]
-                        const int dl = D - 1;
-                        long long a0 = 0, a1 = -1, b0 = 0, b1 = -1;  // empty when x1 < x0
-                        if (ocheb == L) {
-                            a0 = lo[dl];
-                            a1 = hi[dl];
-                        } else {
-                            if (c0[dl] - L >= 0) a0 = a1 = c0[dl] - L;
-                            if (c0[dl] + L <= a.g.cmax[dl]) b0 = b1 = c0[dl] + L;
-                        }
-                        // a run's rows: [st, en) of the cell-ordered rows
-                        auto resolve = [&](long long x0, long long x1, unsigned int& st,
-                                           unsigned int& len) {
-                            st = 0u;
-                            len = 0u;
-                            if (x1 < x0) return;
-                            if (may_skip) {
-                                const float gl = fmaxf(0.0f, axis_gap(x0, x1, u[dl]) -
-                                                                 axis_margin(x1, u[dl]) -
-                                                                 axis_margin(x0, u[dl]));
-                                const float lbr = __fmul_rn(og2 + gl * gl, w2) * (1.0f - 1e-5f);
-                                if (lbr > kth_d) return;
-                            }
-                            if constexpr (DENSE) {
-                                const unsigned int s0 =
-                                    __ldg(a.dstart + base + (unsigned long long)x0);
-                                const unsigned int e0 =
-                                    __ldg(a.dstart + base + (unsigned long long)x1 + 1ull);
-                                if (counting) {
-                                    unsigned int prev = s0;
-                                    for (long long x = x0; x <= x1; ++x) {
-                                        const unsigned int nx =
-                                            __ldg(a.dstart + base + (unsigned long long)x + 1ull);
-                                        cells += nx > prev;
-                                        prev = nx;
-                                    }
-                                }
-                                st = s0;
-                                len = e0 - s0;
-                            } else {
-                                unsigned int s0 = 0xffffffffu, e0 = 0u;
-                                for (long long x = x0; x <= x1; ++x) {
-                                    const unsigned long long key = base + (unsigned long long)x;
-                                    unsigned long long h = mix64(key) & hmask;
-                                    for (unsigned long long probe = 0; probe <= hmask; ++probe) {
-                                        const ulonglong2 e =
-                                            __ldg(reinterpret_cast<const ulonglong2*>(a.slots) + h);
-                                        if (e.x == key) {
-                                            const unsigned int es = (unsigned int)e.y;
-                                            const unsigned int ee = (unsigned int)(e.y >> 32);
-                                            s0 = es < s0 ? es : s0;
-                                            e0 = ee > e0 ? ee : e0;
-                                            ++cells;
-                                            break;
-                                        }
-                                        if (e.x == kEmptyKey) break;
-                                        h = (h + 1ull) & hmask;
-                                    }
-                                }
-                                if (e0 > 0u) {
-                                    st = s0;
-                                    len = e0 - s0;
-                                }
-                            }
-                        };
-                        resolve(a0, a1, sa, la);
-                        resolve(b0, b1, sb, lb_);
-                    }
-                    if (la == 0u && lb_ != 0u) {
-                        sa = sb;
-                        la = lb_;
-                        lb_ = 0u;
-                    }
-                    // flatten the 32 lanes' ranges
-                    const unsigned int tot = la + lb_;
+                if (may_defer && nrows > a.heavy_rows) {
+                    deferred = true;
+                    break;
+                }
+                RowWalk<D> rw;
+                rw.start(b, (unsigned int)lane, 32u);
+                for (unsigned int rb = 0; rb < (unsigned int)nrows; rb += 32u) {
+                    unsigned int sa = 0u, la = 0u, sb = 0u, lb = 0u;
+                    const bool full = tk.count == tk.k;
+                    const float kth_d = __uint_as_float((unsigned)(tk.kth >> 32));
+                    if (rb + lane < (unsigned int)nrows)
+                        row_ranges<D, DENSE>(a, hmask, s, b, rw, L, !counting && full, kth_d,
+                                             counting, sa, la, sb, lb, cells);
+                    rw.advance(b);
+                    // flatten the lanes' ranges
+                    const unsigned int tot = la + lb;
                     cands += tot;
                     unsigned int incl = tot;
 #pragma unroll
@@ -357,6 +675,11 @@ __global__ void __launch_bounds__(kThreads, 2) query_kernel(const QueryArgs a)
                         if (lane >= o) incl += y;
                     }
                     const unsigned int total = __shfl_sync(FULL, incl, 31);
+                    if (total == 0u) continue;
+                    if (may_defer && total > a.heavy_cands) {
+                        deferred = true;
+                        break;
+                    }
                     __syncwarp();
                     s_end[wib][lane] = incl;
                     s_beg[wib][lane] = incl - tot;
@@ -364,56 +687,35 @@ __global__ void __launch_bounds__(kThreads, 2) query_kernel(const QueryArgs a)
                     s_la[wib][lane] = la;
                     s_b[wib][lane] = sb;
                     __syncwarp();
-                    for (unsigned int cb = 0; cb < total; cb += 32) {
+                    for (unsigned int cb = 0; cb < total; cb += 32u) {
                         const unsigned int t = cb + lane;
                         unsigned long long key = kEmptyKey;
-                        const bool open = tk.kth == kEmptyKey;
-                        const float cur_d = __uint_as_float((unsigned)(tk.kth >> 32));
                         if (t < total) {
-                            int lo_l = 0, hi_l = 31;  // the lane whose ranges hold candidate t
-                            while (lo_l < hi_l) {
+                            int lo_l = 0, hi_l = 31;  // the lane whose ranges hold t
+#pragma unroll
+                            for (int it = 0; it < 5; ++it) {
                                 const int mid = (lo_l + hi_l) >> 1;
                                 if (s_end[wib][mid] > t)
                                     hi_l = mid;
                                 else
                                     lo_l = mid + 1;
                             }
-                            const int ow = lo_l;
-                            const unsigned int ln = s_la[wib][ow];
-                            const unsigned int off = t - s_beg[wib][ow];
+                            const unsigned int off = t - s_beg[wib][lo_l];
+                            const unsigned int ln = s_la[wib][lo_l];
                             const unsigned int pos =
-                                off < ln ? s_a[wib][ow] + off : s_b[wib][ow] + (off - ln);
-                            Row<P> row;
-                            row.load(a.rows, pos);
-                            float acc = 0.0f;
-#pragma unroll
-                            for (int j = 0; j < D; ++j) {
-                                const float dj = __fsub_rn(q[j], row.v[j]);
-                                acc = __fadd_rn(acc, __fmul_rn(dj, dj));
-                            }
-                            if (open || acc <= cur_d) {
-                                const unsigned int id = __ldg(a.rid + pos);
-                                key = ((unsigned long long)__float_as_uint(acc) << 32) | id;
-                            }
+                                off < ln ? s_a[wib][lo_l] + off : s_b[wib][lo_l] + (off - ln);
+                            key = candidate_key<D>(a, s, pos, tk.kth == kEmptyKey,
+                                                   __uint_as_float((unsigned)(tk.kth >> 32)));
                         }
-                        unsigned int pass = __ballot_sync(FULL, key < tk.kth);
-                        while (pass) {
-                            const int src = __ffs(pass) - 1;
-                            pass &= pass - 1u;
-                            const unsigned long long x = __shfl_sync(FULL, key, src);
-                            if (x < tk.kth) {
-                                tk.insert(x, lane);
-                                updated = true;
-                            }
-                        }
+                        updated |= offer(tk, key, lane);
                     }
                     __syncwarp();
                 }
+                if (deferred) break;
             }
-
             if (tk.count == tk.k && !updated) break;  // the stop rule of Sec. III.B
-            if (covers) break;                        // every occupied cell seen
-            if (a.max_layers > 0 && L - lmin + 1 >= a.max_layers) {
+            if (b.covers) break;                      // every occupied cell seen
+            if (a.max_layers > 0 && L - s.lmin + 1 >= a.max_layers) {
                 limited = true;
                 if (lane == 0) atomicOr(a.status, kStatusLimit);
                 break;
@@ -421,109 +723,268 @@ __global__ void __launch_bounds__(kThreads, 2) query_kernel(const QueryArgs a)
             ++L;
         }
 
-        // ---- outputs ----
-        const long long obase = qid * (long long)a.k;
+        if (deferred) {
+            // too much work for one warp: the cooperative kernel takes it
+            if (lane == 0) a.heavy_list[atomicAdd(a.heavy_count, 1u)] = (unsigned int)qid;
+        } else {
+            write_outputs(a, qid, tk, limited, lane);
+            if (counting) {
 #pragma unroll
-        for (int i = 0; i < NS; ++i) {
-            const int e = i * 32 + lane;
-            if (e < a.k) {
-                const unsigned long long key = limited ? kEmptyKey : tk.s[i];
-                const bool ok = key != kEmptyKey;
-                a.ids[obase + e] = ok ? (int)(unsigned int)key : -1;
-                if (a.dist2) a.dist2[obase + e] = ok ? __uint_as_float((unsigned)(key >> 32)) : INFINITY;
-            }
-        }
-        const int found = limited ? 0 : tk.count;
-        if (a.mode == 0 && a.pred) {
-            // majority label among the found neighbours, ties to the smallest label
-            unsigned int lab[NS];
-            bool val[NS];
-#pragma unroll
-            for (int i = 0; i < NS; ++i) {
-                val[i] = i * 32 + lane < found;
-                lab[i] = val[i] ? __ldg(a.labels + (unsigned int)tk.s[i]) : 0u;
-            }
-            unsigned long long best = 0ull;
-#pragma unroll
-            for (int i = 0; i < NS; ++i) {
-                int cnt = 0;
-                for (int e = 0; e < found; ++e) {
-                    unsigned int other;
-                    if constexpr (NS == 1) {
-                        other = __shfl_sync(FULL, lab[0], e);
-                    } else {
-                        const unsigned int o0 = __shfl_sync(FULL, lab[0], e & 31);
-                        const unsigned int o1 = __shfl_sync(FULL, lab[1], e & 31);
-                        other = e < 32 ? o0 : o1;
-                    }
-                    cnt += other == lab[i];
+                for (int o = 16; o > 0; o >>= 1) {
+                    cells += __shfl_xor_sync(FULL, cells, o);
+                    cands += __shfl_xor_sync(FULL, cands, o);
                 }
-                if (val[i]) {
-                    const unsigned long long sc = ((unsigned long long)cnt << 32) |
-                                                  (0xffffffffu - (lab[i] ^ 0x80000000u));
-                    best = sc > best ? sc : best;
+                if (lane == 0) {
+                    a.stats[3 * qid + 0] = L + 1;
+                    a.stats[3 * qid + 1] = cells;
+                    a.stats[3 * qid + 2] = cands;
                 }
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long y = __shfl_xor_sync(FULL, best, o);
-                best = y > best ? y : best;
-            }
-            if (lane == 0)
-                static_cast<int*>(a.pred)[qid] =
-                    found ? (int)((0xffffffffu - (unsigned int)best) ^ 0x80000000u) : 0;
-        } else if (a.mode == 1 && a.pred) {
-            // mean of the found neighbours' outputs: double sum in neighbour order
-            float y[NS];
-#pragma unroll
-            for (int i = 0; i < NS; ++i)
-                y[i] = i * 32 + lane < found
-                           ? __uint_as_float(__ldg(a.labels + (unsigned int)tk.s[i]))
-                           : 0.0f;
-            double sum = 0.0;
-            for (int e = 0; e < found; ++e) {
-                float v;
-                if constexpr (NS == 1) {
-                    v = __shfl_sync(FULL, y[0], e);
-                } else {
-                    const float v0 = __shfl_sync(FULL, y[0], e & 31);
-                    const float v1 = __shfl_sync(FULL, y[1], e & 31);
-                    v = e < 32 ? v0 : v1;
-                }
-                sum = __dadd_rn(sum, (double)v);
-            }
-            if (lane == 0)
-                static_cast<float*>(a.pred)[qid] =
-                    found ? __double2float_rn(__ddiv_rn(sum, (double)found)) : __int_as_float(0x7fc00000);
         }
-        if (counting) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                cells += __shfl_xor_sync(FULL, cells, o);
-                cands += __shfl_xor_sync(FULL, cands, o);
-            }
-            if (lane == 0) {
-                a.stats[3 * qid + 0] = L + 1;
-                a.stats[3 * qid + 1] = cells;
-                a.stats[3 * qid + 2] = cands;
-            }
-        }
+        next = __shfl_sync(FULL, next, 0);
     }
 }
 
+// ---------------------------------------------------------------------------
+// The cooperative kernel: one block per deferred query.  Rows and candidates
+// of each layer are spread over the block's warps.  Each warp collects the
+// top k of its own share of the layer's candidates (refusing any key not below
+// the block's k-th key), and at the end of the layer the warps' lists are
+// merged into the block's buffer.  The merged buffer is the top k of the
+// previous buffer and of every candidate of the layer, and the layer
+// "updated" it exactly when it changed, so the stop rule is the one of the
+// sequential walk.  A warp skips with min(its own k-th key, the block's),
+// which is never below the merged k-th key.
+// ---------------------------------------------------------------------------
+
+constexpr int kRoundRows = kThreads;      // rows resolved per round (one per thread)
+constexpr int kRangeCap = 2 * kRoundRows;  // at most two ranges per row
+
 template <int D, int NS, bool DENSE>
-cudaError_t launch_one(const QueryArgs& a, int blocks, cudaStream_t s)
+__global__ void __launch_bounds__(kThreads, 1) heavy_kernel(const QueryArgs a)
 {
-    query_kernel<D, NS, DENSE><<<blocks, kThreads, 0, s>>>(a);
+    __shared__ unsigned long long s_top[64];
+    __shared__ unsigned long long s_loc[kWarps][64];
+    __shared__ unsigned int r_start[kRangeCap];
+    __shared__ unsigned int r_len[kRangeCap];
+    __shared__ unsigned int r_end[kRangeCap];  // inclusive end of each range, flattened
+    __shared__ unsigned int s_wsum[kWarps];
+    __shared__ unsigned int s_nr, s_h;
+    __shared__ int s_count, s_updated;
+
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    unsigned long long hmask = 0ull;
+    if constexpr (!DENSE) hmask = a.gdev->hmask;
+    const unsigned int nheavy = *a.heavy_count;
+
+    for (;;) {
+        if (threadIdx.x == 0) s_h = atomicAdd(a.heavy_cursor, 1u);
+        __syncthreads();
+        const unsigned int h = s_h;
+        if (h >= nheavy) break;
+        const long long qid = (long long)a.heavy_list[h];
+        Query<D> s;
+        query_setup(a, qid, s);
+        if (threadIdx.x < 64) s_top[threadIdx.x] = kEmptyKey;
+        if (threadIdx.x == 0) s_count = 0;
+        __syncthreads();
+
+        TopK<NS> tk;
+        long long L = s.lmin;
+        bool limited = false;
+        for (;;) {
+            // the block's k-th key at the start of the layer, and an empty
+            // list for this warp's share of the layer
+            const unsigned long long gkth = s_count == a.k ? s_top[a.k - 1] : kEmptyKey;
+            tk.init(a.k);
+            Layer<D> b;
+            const float kd0 = __uint_as_float((unsigned)(gkth >> 32));
+            layer_box(a, s, L, gkth != kEmptyKey && kd0 < 1e30f, kd0, b);
+            if (!b.empty) {
+                const unsigned long long nrows = layer_rows(b);
+                if (nrows >= (1ull << 32)) {
+                    limited = true;
+                    if (threadIdx.x == 0) atomicOr(a.status, kStatusLimit);
+                    break;
+                }
+                RowWalk<D> rw;
+                rw.start(b, (unsigned int)threadIdx.x, (unsigned int)kRoundRows);
+                for (unsigned long long rb = 0; rb < nrows; rb += kRoundRows) {
+                    if (threadIdx.x == 0) s_nr = 0u;
+                    __syncthreads();
+                    unsigned int sa = 0u, la = 0u, sb = 0u, lb = 0u;
+                    long long unused = 0;
+                    const unsigned long long ek = tk.kth < gkth ? tk.kth : gkth;
+                    if (rb + threadIdx.x < nrows)
+                        row_ranges<D, DENSE>(a, hmask, s, b, rw, L, ek != kEmptyKey,
+                                             __uint_as_float((unsigned)(ek >> 32)), false, sa, la,
+                                             sb, lb, unused);
+                    rw.advance(b);
+                    // append the non-empty ranges to the block's list
+                    const unsigned int mine = (la > 0u) + (lb > 0u);
+                    unsigned int incl = mine;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const unsigned int y = __shfl_up_sync(FULL, incl, o);
+                        if (lane >= o) incl += y;
+                    }
+                    unsigned int wbase = 0u;
+                    if (lane == 31 && incl) wbase = atomicAdd(&s_nr, incl);
+                    wbase = __shfl_sync(FULL, wbase, 31);
+                    unsigned int at = wbase + incl - mine;
+                    if (la) {
+                        r_start[at] = sa;
+                        r_len[at] = la;
+                        ++at;
+                    }
+                    if (lb) {
+                        r_start[at] = sb;
+                        r_len[at] = lb;
+                    }
+                    __syncthreads();
+                    // flatten the ranges: inclusive prefix of their lengths
+                    const unsigned int nr = s_nr;
+                    const unsigned int i0 = 2u * threadIdx.x, i1 = i0 + 1u;
+                    const unsigned int v0 = i0 < nr ? r_len[i0] : 0u;
+                    const unsigned int v1 = i1 < nr ? r_len[i1] : 0u;
+                    unsigned int x = v0 + v1;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const unsigned int y = __shfl_up_sync(FULL, x, o);
+                        if (lane >= o) x += y;
+                    }
+                    if (lane == 31) s_wsum[wib] = x;
+                    __syncthreads();
+                    unsigned int pre = 0u;
+                    for (int w2 = 0; w2 < wib; ++w2) pre += s_wsum[w2];
+                    x += pre;
+                    if (i0 < nr) r_end[i0] = x - v1;
+                    if (i1 < nr) r_end[i1] = x;
+                    unsigned int total = 0u;
+                    for (int w2 = 0; w2 < kWarps; ++w2) total += s_wsum[w2];
+                    __syncthreads();
+                    // the candidates, 32 per warp at a time
+                    for (unsigned int cb = 32u * wib; cb < total; cb += 32u * kWarps) {
+                        const unsigned int t = cb + lane;
+                        unsigned long long key = kEmptyKey;
+                        if (t < total) {
+                            unsigned int lo_r = 0u, hi_r = nr - 1u;  // first range ending past t
+                            while (lo_r < hi_r) {
+                                const unsigned int mid = (lo_r + hi_r) >> 1;
+                                if (r_end[mid] > t)
+                                    hi_r = mid;
+                                else
+                                    lo_r = mid + 1u;
+                            }
+                            const unsigned int pos = r_start[lo_r] + (t - (r_end[lo_r] - r_len[lo_r]));
+                            const unsigned long long ek = tk.kth < gkth ? tk.kth : gkth;
+                            key = candidate_key<D>(a, s, pos, ek == kEmptyKey,
+                                                   __uint_as_float((unsigned)(ek >> 32)));
+                        }
+                        offer(tk, key, lane, gkth);
+                    }
+                    __syncthreads();
+                }
+            }
+            // merge the warps' buffers into the block's buffer
+#pragma unroll
+            for (int i = 0; i < NS; ++i) s_loc[wib][i * 32 + lane] = tk.s[i];
+            __syncthreads();
+            if (wib == 0) {
+                // start from the block's buffer; the warps' lists hold only
+                // points of this layer, so the merge has no duplicates
+                TopK<NS> g;
+                g.init(a.k);
+#pragma unroll
+                for (int i = 0; i < NS; ++i) g.s[i] = s_top[i * 32 + lane];
+                g.count = s_count;
+                g.refresh_kth();
+                for (int w2 = 0; w2 < kWarps; ++w2) {
+                    if constexpr (NS == 1) {
+                        g.merge32(s_loc[w2][lane], lane);
+                    } else {
+                        for (int e = 0; e < 64; ++e) {
+                            const unsigned long long xk = s_loc[w2][e];
+                            if (!(xk < g.kth)) break;  // the list is sorted
+                            g.insert(xk, lane);
+                        }
+                    }
+                }
+                bool changed = false;
+#pragma unroll
+                for (int i = 0; i < NS; ++i) changed |= g.s[i] != s_top[i * 32 + lane];
+                changed = __any_sync(FULL, changed);
+                __syncwarp();
+#pragma unroll
+                for (int i = 0; i < NS; ++i) s_top[i * 32 + lane] = g.s[i];
+                if (lane == 0) {
+                    s_count = g.count;
+                    s_updated = changed ? 1 : 0;
+                }
+            }
+            __syncthreads();
+            const bool updated = s_updated != 0;
+            const bool full = s_count == a.k;
+            if (full && !updated) break;  // the stop rule of Sec. III.B
+            if (b.covers) break;
+            if (a.max_layers > 0 && L - s.lmin + 1 >= a.max_layers) {
+                limited = true;
+                if (threadIdx.x == 0) atomicOr(a.status, kStatusLimit);
+                break;
+            }
+            ++L;
+        }
+        if (wib == 0) {
+            TopK<NS> g;
+            g.init(a.k);
+#pragma unroll
+            for (int i = 0; i < NS; ++i) g.s[i] = s_top[i * 32 + lane];
+            g.count = s_count;
+            write_outputs(a, qid, g, limited, lane);
+        }
+        __syncthreads();
+    }
+}
+
+template <class Kernel>
+int blocks_per_sm(Kernel k, int& cache)
+{
+    if (cache == 0) {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k, kThreads, 0) != cudaSuccess ||
+            v < 1)
+            v = 1;
+        cache = v;
+    }
+    return cache;
+}
+
+template <int D, int NS, bool DENSE>
+cudaError_t launch_one(const QueryArgs& a, int sms, cudaStream_t s)
+{
+    static int per_sm = 0, per_sm_heavy = 0;
+    long long blocks = (long long)sms * blocks_per_sm(query_kernel<D, NS, DENSE>, per_sm);
+    const long long need = (a.m + kWarps - 1) / kWarps;
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    query_kernel<D, NS, DENSE><<<(int)blocks, kThreads, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || a.heavy_list == nullptr) return e;
+    long long hb = (long long)sms * blocks_per_sm(heavy_kernel<D, NS, DENSE>, per_sm_heavy);
+    if (hb > a.m) hb = a.m;
+    if (hb < 1) hb = 1;
+    heavy_kernel<D, NS, DENSE><<<(int)hb, kThreads, 0, s>>>(a);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 template <int D>
-cudaError_t launch_d(const QueryArgs& a, int blocks, cudaStream_t s)
+cudaError_t launch_d(const QueryArgs& a, int sms, cudaStream_t s)
 {
     const bool two = a.k > 32;
-    if (a.dense) return two ? launch_one<D, 2, true>(a, blocks, s) : launch_one<D, 1, true>(a, blocks, s);
-    return two ? launch_one<D, 2, false>(a, blocks, s) : launch_one<D, 1, false>(a, blocks, s);
+    if (a.dense) return two ? launch_one<D, 2, true>(a, sms, s) : launch_one<D, 1, true>(a, sms, s);
+    return two ? launch_one<D, 2, false>(a, sms, s) : launch_one<D, 1, false>(a, sms, s);
 }
 
 }  // namespace qk

@@ -180,6 +180,15 @@ def test_far_queries_clamped():
     assert_same(got, oracle_run(x, lab, q, 0.05, 6, knn.KNN_VOTE), knn.KNN_VOTE)
 
 
+def test_far_query_fine_grid():
+    """Far queries on a fine grid: cell-unit gaps above 2^64 while distances stay finite."""
+    x, lab, _ = wl.uniform(4000, 1, 2, seed=12, lo=0.0, hi=1e-4)
+    q = np.array([[1e4, 1e4], [-1e4, 5e-5], [5e-5, 3e4], [2e-4, 2e-4]], np.float32)
+    for k in (1, 7):
+        got, _ = gpu_run(x, lab, q, 1e-6, k, knn.KNN_VOTE)
+        assert_same(got, oracle_run(x, lab, q, 1e-6, k, knn.KNN_VOTE), knn.KNN_VOTE)
+
+
 def test_clustered_heavy_cells():
     """Tight clusters: cells with thousands of points next to near-empty space."""
     w = wl.make("skewed_reg", n=200_000, m=3000, w=0.02)
@@ -362,3 +371,42 @@ def test_full_large_cls_sampled():
 
 def test_full_skewed_reg_sampled():
     _sampled_full("skewed_reg", 1500, knn.KNN_QUERY_SORTED)
+
+
+_FORCED_DEFERRAL = r"""
+import numpy as np, torch, oracle
+from paper_2004_02290_gb300 import knn, workloads as wl
+def dev(a): return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+cases = []
+for d, n, m, w, k in [(2, 5000, 300, 0.02, 10), (3, 8000, 300, 0.05, 16), (4, 8000, 200, 0.12, 40),
+                      (1, 3000, 200, 0.002, 7), (6, 3000, 100, 0.35, 5)]:
+    x, lab, q = wl.uniform(n, m, d, seed=500 + d)
+    q = np.concatenate([q, np.full((2, d), -0.4, np.float32), np.full((1, d), 1.3, np.float32)])
+    cases.append((x, lab, q.astype(np.float32), w, k))
+x, lab, q = wl.lattice(20, 2, 200, seed=6)
+cases.append((x, lab, q, 1.0, 9))
+cw = wl.make("skewed_reg", n=100_000, m=1000, w=0.02)
+cases.append((cw.points, cw.labels, cw.queries, cw.w, 16))
+bad = 0
+for x, lab, q, w, k in cases:
+    g = oracle.Grid(x, lab, w)
+    e_ids, e_d2, e_pred = g.query(q, k, 0 if lab.dtype == np.int32 else 1)
+    for table in (knn.KNN_TABLE_DENSE, knn.KNN_TABLE_HASH):
+        idx = knn.knn_build(dev(x), dev(lab), w, table)
+        mode = knn.KNN_VOTE if lab.dtype == np.int32 else knn.KNN_MEAN
+        ids, d2, pred = idx.query(dev(q), k, mode, flags=knn.KNN_QUERY_CHECKED | knn.KNN_QUERY_SORTED)
+        torch.cuda.synchronize()
+        ok = (np.array_equal(ids.cpu().numpy(), e_ids)
+              and np.array_equal(d2.cpu().numpy().view(np.uint32), e_d2.view(np.uint32))
+              and np.array_equal(pred.cpu().numpy().view(np.uint32), e_pred.view(np.uint32)))
+        bad += not ok
+        idx.free()
+print("BAD", bad)
+"""
+
+
+def test_cooperative_kernel_parity():
+    """Every query forced through the cooperative (block-per-query) kernel."""
+    r = _child(_FORCED_DEFERRAL, {"GHN_HEAVY_ROWS": "2", "GHN_HEAVY_CANDS": "8"})
+    assert r.returncode == 0, r.stderr[-3000:]
+    assert "BAD 0" in r.stdout, r.stdout
