@@ -136,6 +136,27 @@ knn_status knn_query(const ghn_index* index, const float* queries, int64_t m, in
 knn_status knn_query_stats(const ghn_index* index, const float* queries, int64_t m, int32_t k,
                            int32_t* ids, float* dist2, int64_t* stats, void* stream);
 
+/*
+ * knn_query_noalloc: knn_query for callers that cannot allocate device memory
+ * while they query (an allocator that already holds the GPU's memory, a loop
+ * that must not pay an allocation's latency or synchronisation, rules that
+ * forbid allocation after start-up).  The paper has no counterpart: this is
+ * a deployment variant of the same query kernels.
+ *   Same arguments and results as knn_query, except:
+ *   - queries, ids, dist2 and pred must be device memory (KNN_EINVAL if not);
+ *   - 0 <= m <= 1048576 (KNN_EINVAL beyond);
+ *   - flags: only KNN_QUERY_CHECKED (the locality order needs sort buffers).
+ * The kernels' scratch lives in a fixed device array of the library (about
+ * 4 MiB, held by every GPU that loads the library until exit).  The first call
+ * on a device looks up that array's address, with the index's device current;
+ * make that first call before any stream capture.  All calls share the array:
+ * calls whose work overlaps on the GPU race on it and must be ordered (one
+ * stream, or synchronised).  No memory is allocated or freed by this call.
+ */
+knn_status knn_query_noalloc(const ghn_index* index, const float* queries, int64_t m, int32_t k,
+                             int32_t mode, int32_t* ids, float* dist2, void* pred, int32_t flags,
+                             void* stream);
+
 /* Shape of the index.  Synchronizes the index's build stream on first use. */
 knn_status knn_index_info(const ghn_index* index, knn_index_info_t* info);
 

@@ -637,6 +637,35 @@ namespace ghn {
 
 void count_launches(long long k) { g_launches += k; }
 
+// Accessors for entry points defined in other translation units.
+void set_error(const char* msg) { set_err("%s", msg); }
+
+int index_device(const ghn_index* x) { return x->device; }
+
+int device_sms(int dev) { return num_sms(dev); }
+
+bool index_has_labels(const ghn_index* x) { return x->labels != nullptr; }
+
+int index_dims(const ghn_index* x) { return x->d; }
+
+void index_query_args(const ghn_index* x, QueryArgs& a)
+{
+    a.g = x->g;
+    a.rows = x->rows;
+    a.rid = x->rid;
+    a.labels = x->labels;
+    a.dstart = x->dstart;
+    a.slots = x->slots;
+    a.bitmap = x->bitmap;
+    a.gdev = x->gdev;
+    a.max_layers = max_layers_env();
+    a.heavy_rows = heavy_rows_env();
+    a.heavy_cands = heavy_cands_env();
+    a.dense = x->table == KNN_TABLE_DENSE;
+}
+
+void index_mark_use(const ghn_index* x, cudaStream_t s) { cudaEventRecord(x->last_use, s); }
+
 cudaError_t launch_query(const QueryArgs& a, int sms, cudaStream_t s)
 {
     const int d = a.g.d;

@@ -138,6 +138,21 @@ struct QueryArgs {
 
 cudaError_t launch_query(const QueryArgs& a, int num_sms, cudaStream_t s);
 
+}  // namespace ghn
+
+struct ghn_index;
+
+namespace ghn {
+
+// Accessors of the index for entry points outside capi.cu.
+void set_error(const char* msg);
+int index_device(const ghn_index* x);
+int device_sms(int dev);
+bool index_has_labels(const ghn_index* x);
+int index_dims(const ghn_index* x);
+void index_query_args(const ghn_index* x, QueryArgs& a);  // the index's part of QueryArgs
+void index_mark_use(const ghn_index* x, cudaStream_t s);
+
 // Persistent launch: as many blocks as fit on `sms` SMs (fewer when m is small).
 cudaError_t launch_query_d12(const QueryArgs& a, int sms, cudaStream_t s);
 cudaError_t launch_query_d34(const QueryArgs& a, int sms, cudaStream_t s);

@@ -39,7 +39,8 @@ class knn_index_info_t(ctypes.Structure):
                 ("has_labels", ctypes.c_int32)]
 
 
-EXPORTED = ["knn_build", "knn_query", "knn_query_stats", "knn_index_info", "knn_index_export",
+EXPORTED = ["knn_build", "knn_query", "knn_query_stats", "knn_query_noalloc", "knn_index_info",
+            "knn_index_export",
             "knn_timing_enable", "knn_timing_read", "knn_kernel_launches", "knn_free",
             "knn_last_error", "knn_abi_version"]
 
@@ -62,6 +63,8 @@ def library(path: str | None = None) -> ctypes.CDLL:
         lib.knn_query.restype = i32
         lib.knn_query_stats.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp]
         lib.knn_query_stats.restype = i32
+        lib.knn_query_noalloc.argtypes = [vp, vp, i64, i32, i32, vp, vp, vp, i32, vp]
+        lib.knn_query_noalloc.restype = i32
         lib.knn_index_info.argtypes = [vp, ctypes.POINTER(knn_index_info_t)]
         lib.knn_index_info.restype = i32
         lib.knn_index_export.argtypes = [vp, vp, vp, vp]
@@ -230,6 +233,25 @@ def knn_query_stats(index: Index, queries, k: int, stream=None):
                                      _stream(stream, queries, ids)))
     del kq, ki, kd, ks
     return ids, dist2, stats
+
+
+def knn_query_noalloc(index: Index, queries, k: int, mode: int, ids, dist2=None, pred=None,
+                      flags: int = 0, stream=None):
+    """knn_query into caller-allocated device tensors, allocating nothing.
+
+    For callers that cannot allocate device memory while they query; the
+    library's fixed scratch array is used instead (m <= 1048576, device
+    buffers only, calls must not overlap on the GPU).
+    """
+    m = int(queries.shape[0])
+    qp, kq = _ptr(queries)
+    ip, ki = _ptr(ids)
+    dp, kd = _ptr(dist2)
+    pp, kp = _ptr(pred)
+    _check(library().knn_query_noalloc(index._h, qp, m, k, mode, ip, dp, pp, flags,
+                                       _stream(stream, queries, ids)))
+    del kq, ki, kd, kp
+    return ids, dist2, pred
 
 
 def knn_free(index: Index):
