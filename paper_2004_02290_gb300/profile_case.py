@@ -21,7 +21,7 @@ def main(argv=None):
     p.add_argument("--config", default="large_cls")
     p.add_argument("--m", type=int, default=None, help="queries (a prefix of the workload's)")
     p.add_argument("--repeat", type=int, default=1)
-    p.add_argument("--unsorted", action="store_true", help="visit queries in input order")
+    p.add_argument("--sorted", action="store_true", help="visit queries in cell order")
     args = p.parse_args(argv)
 
     import torch
@@ -36,7 +36,7 @@ def main(argv=None):
     pts = torch.from_numpy(w.points).to(dev)
     lab = torch.from_numpy(w.labels).to(dev)
     q = torch.from_numpy(w.queries).to(dev)
-    flags = knn.KNN_QUERY_CHECKED | (0 if args.unsorted else knn.KNN_QUERY_SORTED)
+    flags = knn.KNN_QUERY_CHECKED | (knn.KNN_QUERY_SORTED if args.sorted else 0)
     knn.knn_timing_enable(True)
     idx = knn.knn_build(pts, lab, w.w, w.table)
     print("build:", knn.knn_timing_read())

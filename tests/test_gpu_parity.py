@@ -366,11 +366,19 @@ def _sampled_full(name, sample, flags):
 
 
 def test_full_large_cls_sampled():
-    _sampled_full("large_cls", 3000, knn.KNN_QUERY_SORTED)
+    import bench
+
+    _sampled_full("large_cls", 3000, bench.QUERY_FLAGS)
+
+
+def test_full_large_cls_sampled_sorted():
+    _sampled_full("large_cls", 1000, knn.KNN_QUERY_SORTED)
 
 
 def test_full_skewed_reg_sampled():
-    _sampled_full("skewed_reg", 1500, knn.KNN_QUERY_SORTED)
+    import bench
+
+    _sampled_full("skewed_reg", 1500, bench.QUERY_FLAGS)
 
 
 _FORCED_DEFERRAL = r"""
