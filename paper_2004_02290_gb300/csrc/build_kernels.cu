@@ -71,42 +71,76 @@ __global__ void box_partial_kernel(const float* __restrict__ pts, long long tota
     if (t == 0) out[2 * d] = sbad ? 1.0f : 0.0f;
 }
 
-// Reduce the partial boxes; compute the number of cells per dimension from the
-// largest point: ext_j = floor((hi_j - lo_j) / w) + 1 (Eq. 1 is monotone in
-// the coordinate, so no training point has a larger cell coordinate).
-__global__ void box_final_kernel(const float* __restrict__ partial, int nblocks, int d, float w,
-                                 BoxOut* __restrict__ out)
+// Reduce the partial boxes (one block: each thread folds a slice of the
+// partials, then a tree over the block); compute the number of cells per
+// dimension from the largest point: ext_j = floor((hi_j - lo_j) / w) + 1 (Eq. 1
+// is monotone in the coordinate, so no training point has a larger cell).
+constexpr int kBoxFinalThreads = 256;
+
+__global__ void __launch_bounds__(kBoxFinalThreads)
+    box_final_kernel(const float* __restrict__ partial, int nblocks, int d, float w,
+                     BoxOut* __restrict__ out)
 {
-    const int j = threadIdx.x;
-    __shared__ unsigned int flags;
-    if (j == 0) flags = 0u;
-    __syncthreads();
-    if (j < d) {
-        float lo = INFINITY, hi = -INFINITY;
-        bool bad = false;
-        for (int b = 0; b < nblocks; ++b) {
-            const float* p = partial + (size_t)b * (2 * d + 1);
-            lo = fminf(lo, p[j]);
-            hi = fmaxf(hi, p[d + j]);
-            bad |= p[2 * d] != 0.0f;
-        }
-        out->lo[j] = lo;
-        out->hi[j] = hi;
-        long long ext = 0;
-        if (bad || !(lo <= hi)) {
-            atomicOr(&flags, kStatusNonFinite);
-        } else {
-            const float t = __fdiv_rn(__fsub_rn(hi, lo), w);
-            if (!(t < 2147483647.0f)) {
-                atomicOr(&flags, kStatusExtent);
-            } else {
-                ext = (long long)floorf(t) + 1;
+    __shared__ float slo[kMaxD][kBoxFinalThreads];
+    __shared__ float shi[kMaxD][kBoxFinalThreads];
+    __shared__ int sbad;
+    const int t = threadIdx.x;
+    if (t == 0) sbad = 0;
+    float lo[kMaxD], hi[kMaxD];
+#pragma unroll
+    for (int j = 0; j < kMaxD; ++j) {
+        lo[j] = INFINITY;
+        hi[j] = -INFINITY;
+    }
+    bool bad = false;
+    for (int b = t; b < nblocks; b += kBoxFinalThreads) {
+        const float* p = partial + (size_t)b * (2 * d + 1);
+#pragma unroll
+        for (int j = 0; j < kMaxD; ++j) {
+            if (j < d) {
+                lo[j] = fminf(lo[j], p[j]);
+                hi[j] = fmaxf(hi[j], p[d + j]);
             }
         }
-        out->ext[j] = ext;
+        bad |= p[2 * d] != 0.0f;
+    }
+#pragma unroll
+    for (int j = 0; j < kMaxD; ++j) {
+        slo[j][t] = lo[j];
+        shi[j][t] = hi[j];
     }
     __syncthreads();
-    if (j == 0) out->flags = flags;
+    if (bad) sbad = 1;
+    for (int half = kBoxFinalThreads / 2; half > 0; half >>= 1) {
+        if (t < half) {
+#pragma unroll
+            for (int j = 0; j < kMaxD; ++j) {
+                slo[j][t] = fminf(slo[j][t], slo[j][t + half]);
+                shi[j][t] = fmaxf(shi[j][t], shi[j][t + half]);
+            }
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        unsigned int flags = 0u;
+        for (int j = 0; j < d; ++j) {
+            const float l = slo[j][0], h = shi[j][0];
+            out->lo[j] = l;
+            out->hi[j] = h;
+            long long ext = 0;
+            if (sbad || !(l <= h)) {
+                flags |= kStatusNonFinite;
+            } else {
+                const float q = __fdiv_rn(__fsub_rn(h, l), w);
+                if (!(q < 2147483647.0f))
+                    flags |= kStatusExtent;
+                else
+                    ext = (long long)floorf(q) + 1;
+            }
+            out->ext[j] = ext;
+        }
+        out->flags = flags;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -513,7 +547,7 @@ cudaError_t launch_box(const float* pts, long long n, int d, float w, float* par
     const int threads = 64 * d;
     box_partial_kernel<<<partial_blocks, threads, 2 * threads * sizeof(float), s>>>(
         pts, n * d, d, partial);
-    box_final_kernel<<<1, 32, 0, s>>>(partial, partial_blocks, d, w, out);
+    box_final_kernel<<<1, kBoxFinalThreads, 0, s>>>(partial, partial_blocks, d, w, out);
     count_launches(2);
     return cudaGetLastError();
 }
