@@ -345,6 +345,7 @@ knn_status build_impl(const float* points_user, const void* labels_user, long lo
         GridConst& g = x->g;
         memset(&g, 0, sizeof(g));
         g.w = w;
+        g.inv_w = 1.0f / w;
         g.d = d;
         unsigned long long space = 1ull;
         bool overflow = false;

@@ -20,6 +20,7 @@ constexpr unsigned int kStatusExtent = 4u;     // too many cells along one dimen
 struct GridConst {
     float lo[kMaxD];                 // origin: per-dimension minimum
     float w;                         // cell width
+    float inv_w;                     // 1 / w rounded (bounds only, never Eq. 1)
     int d;
     long long cmax[kMaxD];           // largest occupied cell coordinate (extent - 1)
     unsigned long long stride[kMaxD];  // linear id = sum c_j * stride_j, stride_{d-1} = 1

@@ -40,6 +40,7 @@
 
 #include "ghn_internal.cuh"
 
+#include <limits.h>
 #include <math.h>
 
 namespace ghn {
@@ -217,17 +218,17 @@ __device__ __forceinline__ void bitmap_span(const unsigned int* bm, unsigned lon
     }
 }
 
-// Probe the open-addressing table for cell id `key`: its row range, or 0/0.
-__device__ __forceinline__ void hash_lookup(const HashSlot* slots, unsigned long long hmask,
-                                            unsigned long long key, unsigned int& st,
-                                            unsigned int& en, bool& found)
+// Continue probing the open-addressing table for cell id `key` from slot h,
+// whose content e is already loaded: the cell's row range, or 0/0.
+__device__ __forceinline__ void hash_probe(const HashSlot* slots, unsigned long long hmask,
+                                           unsigned long long key, unsigned long long h,
+                                           ulonglong2 e, unsigned int& st, unsigned int& en,
+                                           bool& found)
 {
-    unsigned long long h = mix64(key) & hmask;
     st = 0u;
     en = 0u;
     found = false;
     for (unsigned long long probe = 0; probe <= hmask; ++probe) {
-        const ulonglong2 e = __ldg(reinterpret_cast<const ulonglong2*>(slots) + h);
         if (e.x == key) {
             st = (unsigned int)e.y;
             en = (unsigned int)(e.y >> 32);
@@ -236,7 +237,18 @@ __device__ __forceinline__ void hash_lookup(const HashSlot* slots, unsigned long
         }
         if (e.x == kEmptyKey) return;
         h = (h + 1ull) & hmask;
+        e = __ldg(reinterpret_cast<const ulonglong2*>(slots) + h);
     }
+}
+
+// Probe the table for cell id `key`: its row range, or 0/0.
+__device__ __forceinline__ void hash_lookup(const HashSlot* slots, unsigned long long hmask,
+                                            unsigned long long key, unsigned int& st,
+                                            unsigned int& en, bool& found)
+{
+    const unsigned long long h = mix64(key) & hmask;
+    hash_probe(slots, hmask, key, h, __ldg(reinterpret_cast<const ulonglong2*>(slots) + h), st,
+               en, found);
 }
 
 // Row range of the occupied cells among the cells [base + x0, base + x1] of one
@@ -270,16 +282,14 @@ __device__ __forceinline__ void resolve_run(const QueryArgs& a, unsigned long lo
         bitmap_span(a.bitmap, i0, i1, f, l, cnt, counting);
         cells += cnt;
         if (f > i1) return;
+        // the first slots of both cells are loaded together
+        const unsigned long long hf = mix64(f) & hmask, hl = mix64(l) & hmask;
+        const ulonglong2 ef = __ldg(reinterpret_cast<const ulonglong2*>(a.slots) + hf);
+        const ulonglong2 el = __ldg(reinterpret_cast<const ulonglong2*>(a.slots) + hl);
         unsigned int s0, e0, s1, e1;
         bool ok0, ok1;
-        hash_lookup(a.slots, hmask, f, s0, e0, ok0);
-        if (l == f) {
-            s1 = s0;
-            e1 = e0;
-            ok1 = ok0;
-        } else {
-            hash_lookup(a.slots, hmask, l, s1, e1, ok1);
-        }
+        hash_probe(a.slots, hmask, f, hf, ef, s0, e0, ok0);
+        hash_probe(a.slots, hmask, l, hl, el, s1, e1, ok1);
         if (ok0 && ok1) {
             st = s0;
             len = e1 - s0;
@@ -362,16 +372,22 @@ __device__ __forceinline__ void layer_box(const QueryArgs& a, const Query<D>& s,
         b.covers &= (s.c0[j] - L <= 0) && (s.c0[j] + L >= a.g.cmax[j]);
     }
     if (!skipping) return;
-    // a cell farther than kd along one axis cannot hold a point that enters
-    const float r = __fdiv_rn(sqrtf(kd), a.g.w) * (1.0f + 2e-5f);
+    // a cell farther than kd along one axis cannot hold a point that enters;
+    // the radius r = sqrt(kd) / w in cell units is taken with fast approximate
+    // operations (errors near 1e-6) and widened by 1e-4
+    const float r = (kd > 0.0f ? kd * rsqrtf(kd) : 0.0f) * a.g.inv_w * (1.0f + 1e-4f);
     bool shell = false;
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-        const float m = 1e-6f * (fabsf(s.u[j]) + r) + 1e-3f;
-        const long long a0 = (long long)fminf(fmaxf(floorf(s.u[j] - r - m), -4e18f), 4e18f);
-        const long long a1 = (long long)fminf(fmaxf(floorf(s.u[j] + r + m), -4e18f), 4e18f);
-        if (a0 > b.lo[j]) b.lo[j] = a0 > b.hi[j] ? b.hi[j] + 1 : (int)a0;
-        if (a1 < b.hi[j]) b.hi[j] = a1 < b.lo[j] ? b.lo[j] - 1 : (int)a1;
+        const float m = 1e-5f * (fabsf(s.u[j]) + r) + 1e-3f;
+        const float a0f = floorf(s.u[j] - r - m), a1f = floorf(s.u[j] + r + m);
+        // beyond the int range the clip would not tighten the box anyway
+        const int a0 = a0f <= -2147483520.0f ? INT_MIN
+                       : a0f >= 2147483520.0f ? INT_MAX : (int)a0f;
+        const int a1 = a1f >= 2147483520.0f ? INT_MAX
+                       : a1f <= -2147483520.0f ? INT_MIN : (int)a1f;
+        if (a0 > b.lo[j]) b.lo[j] = a0 > b.hi[j] ? b.hi[j] + 1 : a0;
+        if (a1 < b.hi[j]) b.hi[j] = a1 < b.lo[j] ? b.lo[j] - 1 : a1;
         b.empty |= b.lo[j] > b.hi[j];
         shell |= (s.c0[j] - L >= b.lo[j] && s.c0[j] - L <= b.hi[j]) ||
                  (s.c0[j] + L >= b.lo[j] && s.c0[j] + L <= b.hi[j]);
@@ -603,8 +619,36 @@ __device__ __forceinline__ void write_outputs(const QueryArgs& a, long long qid,
 // The warp kernel: one warp per query
 // ---------------------------------------------------------------------------
 
+// Row position of flattened candidate t: the lane whose ranges hold it by
+// binary search over the lanes' inclusive ends.
+__device__ __forceinline__ unsigned int search_pos(const unsigned int* end, const unsigned int* beg,
+                                                   const unsigned int* sa, const unsigned int* la,
+                                                   const unsigned int* sb, unsigned int t)
+{
+    int lo_l = 0, hi_l = 31;
+#pragma unroll
+    for (int it = 0; it < 5; ++it) {
+        const int mid = (lo_l + hi_l) >> 1;
+        if (end[mid] > t)
+            hi_l = mid;
+        else
+            lo_l = mid + 1;
+    }
+    const unsigned int off = t - beg[lo_l];
+    const unsigned int ln = la[lo_l];
+    return off < ln ? sa[lo_l] + off : sb[lo_l] + (off - ln);
+}
+
+// Resident blocks per SM the warp kernel is compiled for.  The walk is bound by
+// memory latency, so more resident warps pay even when the register cap
+// spills a little to L1 (measured on the d=3 and d=4 workloads).
+template <int D, int NS>
+struct MinBlocks {
+    static constexpr int value = (D <= 4 && NS == 1) ? 8 : 2;
+};
+
 template <int D, int NS, bool DENSE>
-__global__ void __launch_bounds__(kThreads, (D <= 4 && NS == 1) ? 3 : 2)
+__global__ void __launch_bounds__(kThreads, (MinBlocks<D, NS>::value))
     query_kernel(const QueryArgs a)
 {
     __shared__ unsigned int s_end[kWarps][32];  // inclusive end of each lane's ranges
@@ -687,25 +731,39 @@ __global__ void __launch_bounds__(kThreads, (D <= 4 && NS == 1) ? 3 : 2)
                     s_la[wib][lane] = la;
                     s_b[wib][lane] = sb;
                     __syncwarp();
+                    // chunks of 32 candidates; the next chunk's rows are loaded
+                    // while the current one is offered to the buffer
+                    constexpr int P = row_floats(D);
+                    auto locate = [&](unsigned int t) -> unsigned int {
+                        return search_pos(s_end[wib], s_beg[wib], s_a[wib], s_la[wib], s_b[wib], t);
+                    };
+                    Row<P> nrow;
+                    unsigned int nrid = 0u;
+                    if (lane < total) {
+                        const unsigned int pos = locate(lane);
+                        nrow.load(a.rows, pos);
+                        nrid = __ldg(a.rid + pos);
+                    }
                     for (unsigned int cb = 0; cb < total; cb += 32u) {
                         const unsigned int t = cb + lane;
+                        const Row<P> row = nrow;
+                        const unsigned int rid = nrid;
+                        if (t + 32u < total) {
+                            const unsigned int pos = locate(t + 32u);
+                            nrow.load(a.rows, pos);
+                            nrid = __ldg(a.rid + pos);
+                        }
                         unsigned long long key = kEmptyKey;
                         if (t < total) {
-                            int lo_l = 0, hi_l = 31;  // the lane whose ranges hold t
+                            float acc = 0.0f;
 #pragma unroll
-                            for (int it = 0; it < 5; ++it) {
-                                const int mid = (lo_l + hi_l) >> 1;
-                                if (s_end[wib][mid] > t)
-                                    hi_l = mid;
-                                else
-                                    lo_l = mid + 1;
+                            for (int j = 0; j < D; ++j) {
+                                const float dj = __fsub_rn(s.q[j], row.v[j]);
+                                acc = __fadd_rn(acc, __fmul_rn(dj, dj));
                             }
-                            const unsigned int off = t - s_beg[wib][lo_l];
-                            const unsigned int ln = s_la[wib][lo_l];
-                            const unsigned int pos =
-                                off < ln ? s_a[wib][lo_l] + off : s_b[wib][lo_l] + (off - ln);
-                            key = candidate_key<D>(a, s, pos, tk.kth == kEmptyKey,
-                                                   __uint_as_float((unsigned)(tk.kth >> 32)));
+                            if (tk.kth == kEmptyKey ||
+                                acc <= __uint_as_float((unsigned)(tk.kth >> 32)))
+                                key = ((unsigned long long)__float_as_uint(acc) << 32) | rid;
                         }
                         updated |= offer(tk, key, lane);
                     }
