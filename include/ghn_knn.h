@@ -157,6 +157,56 @@ knn_status knn_query_noalloc(const ghn_index* index, const float* queries, int64
                              int32_t mode, int32_t* ids, float* dist2, void* pred, int32_t flags,
                              void* stream);
 
+/*
+ * Batches of independent indexes (many small and large problems at once).
+ * Each index of a batch is the method of knn_build / knn_query on its own
+ * points with its own cell width (Sec. III.A-B); the batch builds all of them
+ * in one pass over their points (one host synchronisation for all boxes) and
+ * queries all of them in one persistent launch per dimension.  Results equal
+ * those of knn_build + knn_query on each index.
+ */
+typedef struct ghn_batch ghn_batch; /* opaque; owns the device memory of its indexes */
+typedef struct ghn_plan ghn_plan;   /* a captured batch query (CUDA graph) */
+
+/*
+ * knn_batch_build: build `count` indexes (1 <= count <= 65536).
+ *   points[i]      device, n[i]*d[i] float32, row-major.
+ *   labels         NULL, or an array whose entry i is a device pointer to
+ *                  n[i] 32-bit outputs, or NULL for index i.
+ *   n, d, cell_width, table   host arrays of count entries, as in knn_build
+ *                  (table may be NULL: KNN_TABLE_AUTO for every index).
+ * The total number of points must be below 2^31.  Errors as knn_build, and
+ * KNN_EINVAL when the cell ids of the batch need more than 63 bits.
+ */
+knn_status knn_batch_build(int32_t count, const float* const* points, const void* const* labels,
+                           const int64_t* n, const int32_t* d, const float* cell_width,
+                           const int32_t* table, void* stream, ghn_batch** out);
+
+/* Shape of index i of the batch (table_slots: dense entries, 0 for hash). */
+knn_status knn_batch_info(const ghn_batch* batch, int32_t i, knn_index_info_t* info);
+
+/*
+ * knn_batch_query: query every index of the batch (host arrays of count
+ * entries; every data pointer is device memory; m[i] may be 0).  Outputs of
+ * index i as knn_query's.  flags: KNN_QUERY_CHECKED only.
+ */
+knn_status knn_batch_query(const ghn_batch* batch, const float* const* queries, const int64_t* m,
+                           const int32_t* k, const int32_t* mode, int32_t* const* ids,
+                           float* const* dist2, void* const* pred, int32_t flags, void* stream);
+
+/*
+ * knn_batch_plan / knn_batch_run: the same query captured once in a CUDA
+ * graph (the buffers are fixed at plan time) and replayed by each run.
+ * A plan must be freed before its batch.  knn_batch_run flags:
+ * KNN_QUERY_CHECKED (synchronize and return the status) or 0.
+ */
+knn_status knn_batch_plan(const ghn_batch* batch, const float* const* queries, const int64_t* m,
+                          const int32_t* k, const int32_t* mode, int32_t* const* ids,
+                          float* const* dist2, void* const* pred, ghn_plan** out);
+knn_status knn_batch_run(ghn_plan* plan, int32_t flags, void* stream);
+void knn_plan_free(ghn_plan* plan);   /* NULL-safe */
+void knn_batch_free(ghn_batch* batch); /* NULL-safe; waits for work that uses it */
+
 /* Shape of the index.  Synchronizes the index's build stream on first use. */
 knn_status knn_index_info(const ghn_index* index, knn_index_info_t* info);
 

@@ -1,0 +1,86 @@
+"""Autotuner for the cell width of each index of a problem set.
+
+The paper measures cells from the data (Sec. III.A); the library takes the
+width from the caller.  For a problem set, the tuner picks each index's width
+by measurement on the GPU: for a few candidate widths around a starting guess
+it builds the index and times a sample of the queries, and keeps the width of
+the least estimated time (build + sampled query time scaled to all queries).
+The kernels' tile shape (one warp per query, 32-candidate chunks, the
+number of resident blocks) is fixed by the design and its occupancy sweep.
+
+Every candidate runs through the same library calls as a normal query, so
+the chosen width is an input like any other: the oracle takes it unchanged.
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+
+import numpy as np
+
+from . import knn
+
+
+@dataclasses.dataclass
+class Choice:
+    width: float
+    est_ms: float
+    tried: list  # (width, est_ms)
+
+
+def start_width(points: np.ndarray, k: int) -> float:
+    """A first guess: cells holding about max(2, k/2) points if the data filled its box."""
+    n, d = points.shape
+    span = points.max(axis=0).astype(np.float64) - points.min(axis=0).astype(np.float64)
+    span = np.maximum(span, 1e-12)
+    vol = float(np.prod(span))
+    occ = max(2.0, k / 2.0)
+    return float(np.float32((vol * occ / n) ** (1.0 / d)))
+
+
+def tune_width(points, labels, queries, k: int, mode: int, factors=(0.5, 0.71, 1.0, 1.41, 2.0),
+               sample: int = 4096, dev=None) -> Choice:
+    """Width of least estimated build + query time for one problem (GPU)."""
+    import torch
+
+    dev = dev or torch.device("cuda:0")
+    pts_h = np.ascontiguousarray(points, np.float32)
+    w0 = start_width(pts_h, k)
+    pts = torch.from_numpy(pts_h).to(dev)
+    lab = torch.from_numpy(np.ascontiguousarray(labels)).to(dev) if labels is not None else None
+    m = int(queries.shape[0])
+    s = min(sample, m)
+    rng = np.random.default_rng(0)
+    pick = np.sort(rng.choice(m, size=s, replace=False)) if s < m else np.arange(m)
+    q = torch.from_numpy(np.ascontiguousarray(queries[pick], np.float32)).to(dev)
+    tried = []
+    best = None
+    stream = torch.cuda.current_stream(dev)
+    for f in factors:
+        w = float(np.float32(w0 * f))
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        try:
+            ev[0].record(stream)
+            idx = knn.knn_build(pts, lab, w)
+            ev[1].record(stream)
+            idx.query(q, k, mode if lab is not None else knn.KNN_NONE)
+            ev[2].record(stream)
+            ev[2].synchronize()
+            idx.free()
+        except knn.KnnError:
+            continue  # a width the index cannot hold (grid too fine)
+        est = ev[0].elapsed_time(ev[1]) + ev[1].elapsed_time(ev[2]) * (m / s)
+        tried.append((w, est))
+        if best is None or est < best[1]:
+            best = (w, est)
+    if best is None:
+        raise RuntimeError("no candidate width could be built")
+    return Choice(width=best[0], est_ms=best[1], tried=tried)
+
+
+def tune_batch(problems, dev=None, factors=(0.5, 0.71, 1.0, 1.41, 2.0)):
+    """Widths for every problem; returns (widths, seconds spent, choices)."""
+    t0 = time.perf_counter()
+    choices = [tune_width(p.points, p.labels, p.queries, p.k, p.mode, factors=factors, dev=dev)
+               for p in problems]
+    return [c.width for c in choices], time.perf_counter() - t0, choices

@@ -702,6 +702,14 @@ cudaError_t launch_bitmap(const unsigned long long* cell_key, const GridDev* gde
     return cudaGetLastError();
 }
 
+cudaError_t launch_hash_clear(HashSlot* slots, const GridDev* gdev, unsigned long long max_slots,
+                              cudaStream_t s)
+{
+    hash_clear_kernel<<<grid_for((long long)max_slots, 256), 256, 0, s>>>(slots, gdev);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gather(const float* pts, long long n, int d, const unsigned int* order,
                           float* rows, cudaStream_t s)
 {

@@ -667,6 +667,33 @@ void index_query_args(const ghn_index* x, QueryArgs& a)
 
 void index_mark_use(const ghn_index* x, cudaStream_t s) { cudaEventRecord(x->last_use, s); }
 
+cudaError_t launch_batch_query(const BatchArgs& g, int sms, cudaStream_t s)
+{
+    count_launches(1);
+    if (g.d <= 2) return launch_batch_query_d12(g, sms, s);
+    if (g.d <= 4) return launch_batch_query_d34(g, sms, s);
+    if (g.d <= 6) return launch_batch_query_d56(g, sms, s);
+    return launch_batch_query_d78(g, sms, s);
+}
+
+knn_status device_alloc(void** p, size_t bytes, cudaStream_t s, const char* what)
+{
+    char* c = nullptr;
+    knn_status st = dalloc(&c, bytes, s, what);
+    *p = c;
+    return st;
+}
+
+void device_free(void* p, cudaStream_t s)
+{
+    if (p) cudaFreeAsync(p, s);
+}
+
+unsigned int heavy_rows_default() { return heavy_rows_env(); }
+unsigned int heavy_cands_default() { return heavy_cands_env(); }
+long long max_layers_default() { return max_layers_env(); }
+void tune_device_pool(int dev) { tune_pool(dev); }
+
 cudaError_t launch_query(const QueryArgs& a, int sms, cudaStream_t s)
 {
     const int d = a.g.d;

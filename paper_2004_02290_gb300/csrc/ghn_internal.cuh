@@ -99,6 +99,10 @@ cudaError_t launch_hash_table(const unsigned long long* cell_key, const unsigned
                               const GridDev* gdev, HashSlot* slots, unsigned long long max_slots,
                               cudaStream_t s);
 
+// Empty every slot of a table whose capacity the device computed (gdev->hmask + 1).
+cudaError_t launch_hash_clear(HashSlot* slots, const GridDev* gdev, unsigned long long max_slots,
+                              cudaStream_t s);
+
 // Occupancy bitmap over the box (bit id set when cell id holds a point);
 // `words` 32-bit words, zeroed here.
 cudaError_t launch_bitmap(const unsigned long long* cell_key, const GridDev* gdev,
@@ -123,6 +127,7 @@ struct QueryArgs {
     const unsigned int* dstart;     // dense: ncell_space + 1 row offsets
     const HashSlot* slots;          // hash table
     const unsigned int* bitmap;     // hash: one bit per cell of the box, or null
+    unsigned long long key_prefix;  // hash keys are key_prefix | cell id (0 for one index)
     const GridDev* gdev;
     unsigned long long* counter;    // work counter, zero at launch
     unsigned int* status;           // status bits
@@ -139,6 +144,26 @@ struct QueryArgs {
 
 cudaError_t launch_query(const QueryArgs& a, int num_sms, cudaStream_t s);
 
+// A group of indexes of one dimension queried in one persistent launch: the
+// queries of index i are the group's queries qoff[i] .. qoff[i+1]-1.
+struct BatchArgs {
+    const QueryArgs* args;           // device: one per index of the group
+    const unsigned long long* qoff;  // device: count + 1 prefix offsets
+    int count;
+    int d;
+    unsigned long long total;        // queries of the group
+    unsigned long long* counter;     // zero at launch
+    unsigned int* heavy_list;        // total entries, or null: no deferral
+    unsigned int* heavy_count;       // zero at launch
+    unsigned int* heavy_cursor;      // zero at launch
+};
+
+cudaError_t launch_batch_query(const BatchArgs& g, int num_sms, cudaStream_t s);
+cudaError_t launch_batch_query_d12(const BatchArgs& g, int sms, cudaStream_t s);
+cudaError_t launch_batch_query_d34(const BatchArgs& g, int sms, cudaStream_t s);
+cudaError_t launch_batch_query_d56(const BatchArgs& g, int sms, cudaStream_t s);
+cudaError_t launch_batch_query_d78(const BatchArgs& g, int sms, cudaStream_t s);
+
 }  // namespace ghn
 
 struct ghn_index;
@@ -153,6 +178,14 @@ bool index_has_labels(const ghn_index* x);
 int index_dims(const ghn_index* x);
 void index_query_args(const ghn_index* x, QueryArgs& a);  // the index's part of QueryArgs
 void index_mark_use(const ghn_index* x, cudaStream_t s);
+
+// Allocation through the library's pool (with the GHN_FAIL_ALLOC_AT injector).
+int device_alloc(void** p, size_t bytes, cudaStream_t s, const char* what);
+void device_free(void* p, cudaStream_t s);
+unsigned int heavy_rows_default();
+unsigned int heavy_cands_default();
+long long max_layers_default();
+void tune_device_pool(int dev);
 
 // Persistent launch: as many blocks as fit on `sms` SMs (fewer when m is small).
 cudaError_t launch_query_d12(const QueryArgs& a, int sms, cudaStream_t s);

@@ -13,4 +13,13 @@ cudaError_t launch_query_d12(const QueryArgs& a, int sms, cudaStream_t s)
     }
 }
 
+cudaError_t launch_batch_query_d12(const BatchArgs& g, int sms, cudaStream_t s)
+{
+    switch (g.d) {
+    case 1: return qk::launch_batch_d<1>(g, sms, s);
+    case 2: return qk::launch_batch_d<2>(g, sms, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace ghn

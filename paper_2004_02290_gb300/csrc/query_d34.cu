@@ -13,4 +13,13 @@ cudaError_t launch_query_d34(const QueryArgs& a, int sms, cudaStream_t s)
     }
 }
 
+cudaError_t launch_batch_query_d34(const BatchArgs& g, int sms, cudaStream_t s)
+{
+    switch (g.d) {
+    case 3: return qk::launch_batch_d<3>(g, sms, s);
+    case 4: return qk::launch_batch_d<4>(g, sms, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace ghn

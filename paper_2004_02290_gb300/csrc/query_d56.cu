@@ -13,4 +13,13 @@ cudaError_t launch_query_d56(const QueryArgs& a, int sms, cudaStream_t s)
     }
 }
 
+cudaError_t launch_batch_query_d56(const BatchArgs& g, int sms, cudaStream_t s)
+{
+    switch (g.d) {
+    case 5: return qk::launch_batch_d<5>(g, sms, s);
+    case 6: return qk::launch_batch_d<6>(g, sms, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace ghn

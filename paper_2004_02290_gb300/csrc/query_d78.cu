@@ -13,4 +13,13 @@ cudaError_t launch_query_d78(const QueryArgs& a, int sms, cudaStream_t s)
     }
 }
 
+cudaError_t launch_batch_query_d78(const BatchArgs& g, int sms, cudaStream_t s)
+{
+    switch (g.d) {
+    case 7: return qk::launch_batch_d<7>(g, sms, s);
+    case 8: return qk::launch_batch_d<8>(g, sms, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace ghn

@@ -282,7 +282,10 @@ __device__ __forceinline__ void resolve_run(const QueryArgs& a, unsigned long lo
         bitmap_span(a.bitmap, i0, i1, f, l, cnt, counting);
         cells += cnt;
         if (f > i1) return;
-        // the first slots of both cells are loaded together
+        // the first slots of both cells are loaded together; a batch of
+        // indexes shares one table, keyed by index and cell id
+        f |= a.key_prefix;
+        l |= a.key_prefix;
         const unsigned long long hf = mix64(f) & hmask, hl = mix64(l) & hmask;
         const ulonglong2 ef = __ldg(reinterpret_cast<const ulonglong2*>(a.slots) + hf);
         const ulonglong2 el = __ldg(reinterpret_cast<const ulonglong2*>(a.slots) + hl);
@@ -299,7 +302,7 @@ __device__ __forceinline__ void resolve_run(const QueryArgs& a, unsigned long lo
         for (unsigned long long i = i0; i <= i1; ++i) {
             unsigned int cs, ce;
             bool ok;
-            hash_lookup(a.slots, hmask, i, cs, ce, ok);
+            hash_lookup(a.slots, hmask, i | a.key_prefix, cs, ce, ok);
             if (ok) {
                 s0 = cs < s0 ? cs : s0;
                 e0 = ce > e0 ? ce : e0;
@@ -647,22 +650,152 @@ struct MinBlocks {
     static constexpr int value = (D <= 4 && NS == 1) ? 8 : 2;
 };
 
+// Per-warp shared memory of the walk: the lanes' ranges of one row batch.
+struct WarpSmem {
+    unsigned int end[32];  // inclusive end of each lane's ranges, flattened
+    unsigned int beg[32];  // exclusive start of each lane's ranges
+    unsigned int a[32];    // first range: start
+    unsigned int la[32];   // first range: length
+    unsigned int b[32];    // second range: start
+};
+
+// One query by one warp.  Returns true when the query was deferred to the
+// cooperative kernel (nothing written); otherwise its outputs are written.
+template <int D, int NS, bool DENSE>
+__device__ __forceinline__ bool walk_query(const QueryArgs& a, long long qid, WarpSmem& sm,
+                                           int lane, bool counting, bool may_defer)
+{
+    unsigned long long hmask = 0ull;
+    if constexpr (!DENSE) hmask = a.gdev->hmask;
+    Query<D> s;
+    query_setup(a, qid, s);
+    TopK<NS> tk;
+    tk.init(a.k);
+    long long L = s.lmin;
+    long long cells = 0, cands = 0;
+    bool limited = !s.finite, deferred = false;
+    if (!s.finite && lane == 0) atomicOr(a.status, kStatusNonFinite);
+
+    while (!limited) {
+        Layer<D> b;
+        const float kd0 = __uint_as_float((unsigned)(tk.kth >> 32));
+        layer_box(a, s, L, !counting && tk.count == tk.k && kd0 < 1e30f, kd0, b);
+        bool updated = false;
+        if (!b.empty) {
+            const unsigned long long nrows = layer_rows(b);
+            if (nrows >= (1ull << 32)) {
+                limited = true;
+                if (lane == 0) atomicOr(a.status, kStatusLimit);
+                break;
+            }
+            if (may_defer && nrows > a.heavy_rows) {
+                deferred = true;
+                break;
+            }
+            RowWalk<D> rw;
+            rw.start(b, (unsigned int)lane, 32u);
+            for (unsigned int rb = 0; rb < (unsigned int)nrows; rb += 32u) {
+                unsigned int sa = 0u, la = 0u, sb = 0u, lb = 0u;
+                const bool full = tk.count == tk.k;
+                const float kth_d = __uint_as_float((unsigned)(tk.kth >> 32));
+                if (rb + lane < (unsigned int)nrows)
+                    row_ranges<D, DENSE>(a, hmask, s, b, rw, L, !counting && full, kth_d, counting,
+                                         sa, la, sb, lb, cells);
+                rw.advance(b);
+                // flatten the lanes' ranges
+                const unsigned int tot = la + lb;
+                cands += tot;
+                unsigned int incl = tot;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned int y = __shfl_up_sync(FULL, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const unsigned int total = __shfl_sync(FULL, incl, 31);
+                if (total == 0u) continue;
+                if (may_defer && total > a.heavy_cands) {
+                    deferred = true;
+                    break;
+                }
+                __syncwarp();
+                sm.end[lane] = incl;
+                sm.beg[lane] = incl - tot;
+                sm.a[lane] = sa;
+                sm.la[lane] = la;
+                sm.b[lane] = sb;
+                __syncwarp();
+                // chunks of 32 candidates; the next chunk's rows are loaded
+                // while the current one is offered to the buffer
+                constexpr int P = row_floats(D);
+                Row<P> nrow;
+                unsigned int nrid = 0u;
+                if (lane < total) {
+                    const unsigned int pos = search_pos(sm.end, sm.beg, sm.a, sm.la, sm.b, lane);
+                    nrow.load(a.rows, pos);
+                    nrid = __ldg(a.rid + pos);
+                }
+                for (unsigned int cb = 0; cb < total; cb += 32u) {
+                    const unsigned int t = cb + lane;
+                    const Row<P> row = nrow;
+                    const unsigned int rid = nrid;
+                    if (t + 32u < total) {
+                        const unsigned int pos =
+                            search_pos(sm.end, sm.beg, sm.a, sm.la, sm.b, t + 32u);
+                        nrow.load(a.rows, pos);
+                        nrid = __ldg(a.rid + pos);
+                    }
+                    unsigned long long key = kEmptyKey;
+                    if (t < total) {
+                        float acc = 0.0f;
+#pragma unroll
+                        for (int j = 0; j < D; ++j) {
+                            const float dj = __fsub_rn(s.q[j], row.v[j]);
+                            acc = __fadd_rn(acc, __fmul_rn(dj, dj));
+                        }
+                        if (tk.kth == kEmptyKey || acc <= __uint_as_float((unsigned)(tk.kth >> 32)))
+                            key = ((unsigned long long)__float_as_uint(acc) << 32) | rid;
+                    }
+                    updated |= offer(tk, key, lane);
+                }
+                __syncwarp();
+            }
+            if (deferred) break;
+        }
+        if (tk.count == tk.k && !updated) break;  // the stop rule of Sec. III.B
+        if (b.covers) break;                      // every occupied cell seen
+        if (a.max_layers > 0 && L - s.lmin + 1 >= a.max_layers) {
+            limited = true;
+            if (lane == 0) atomicOr(a.status, kStatusLimit);
+            break;
+        }
+        ++L;
+    }
+    if (deferred) return true;
+    write_outputs(a, qid, tk, limited, lane);
+    if (counting) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            cells += __shfl_xor_sync(FULL, cells, o);
+            cands += __shfl_xor_sync(FULL, cands, o);
+        }
+        if (lane == 0) {
+            a.stats[3 * qid + 0] = L + 1;
+            a.stats[3 * qid + 1] = cells;
+            a.stats[3 * qid + 2] = cands;
+        }
+    }
+    return false;
+}
+
 template <int D, int NS, bool DENSE>
 __global__ void __launch_bounds__(kThreads, (MinBlocks<D, NS>::value))
     query_kernel(const QueryArgs a)
 {
-    __shared__ unsigned int s_end[kWarps][32];  // inclusive end of each lane's ranges
-    __shared__ unsigned int s_beg[kWarps][32];  // exclusive start of each lane's ranges
-    __shared__ unsigned int s_a[kWarps][32];    // first range: start
-    __shared__ unsigned int s_la[kWarps][32];   // first range: length
-    __shared__ unsigned int s_b[kWarps][32];    // second range: start
-
+    __shared__ WarpSmem sm[kWarps];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const bool counting = a.stats != nullptr;
     const bool may_defer = !counting && a.heavy_list != nullptr;
-    unsigned long long hmask = 0ull;
-    if constexpr (!DENSE) hmask = a.gdev->hmask;
 
     // the next query is claimed one query ahead, so the atomic's latency
     // overlaps the current query's work
@@ -673,131 +806,9 @@ __global__ void __launch_bounds__(kThreads, (MinBlocks<D, NS>::value))
         const unsigned long long qi = next;
         if (lane == 0) next = atomicAdd(a.counter, 1ull);
         const long long qid = a.order ? (long long)a.order[qi] : (long long)qi;
-
-        Query<D> s;
-        query_setup(a, qid, s);
-        TopK<NS> tk;
-        tk.init(a.k);
-        long long L = s.lmin;
-        long long cells = 0, cands = 0;
-        bool limited = !s.finite, deferred = false;
-        if (!s.finite && lane == 0) atomicOr(a.status, kStatusNonFinite);
-
-        while (!limited) {
-            Layer<D> b;
-            const float kd0 = __uint_as_float((unsigned)(tk.kth >> 32));
-            layer_box(a, s, L, !counting && tk.count == tk.k && kd0 < 1e30f, kd0, b);
-            bool updated = false;
-            if (!b.empty) {
-                const unsigned long long nrows = layer_rows(b);
-                if (nrows >= (1ull << 32)) {
-                    limited = true;
-                    if (lane == 0) atomicOr(a.status, kStatusLimit);
-                    break;
-                }
-                if (may_defer && nrows > a.heavy_rows) {
-                    deferred = true;
-                    break;
-                }
-                RowWalk<D> rw;
-                rw.start(b, (unsigned int)lane, 32u);
-                for (unsigned int rb = 0; rb < (unsigned int)nrows; rb += 32u) {
-                    unsigned int sa = 0u, la = 0u, sb = 0u, lb = 0u;
-                    const bool full = tk.count == tk.k;
-                    const float kth_d = __uint_as_float((unsigned)(tk.kth >> 32));
-                    if (rb + lane < (unsigned int)nrows)
-                        row_ranges<D, DENSE>(a, hmask, s, b, rw, L, !counting && full, kth_d,
-                                             counting, sa, la, sb, lb, cells);
-                    rw.advance(b);
-                    // flatten the lanes' ranges
-                    const unsigned int tot = la + lb;
-                    cands += tot;
-                    unsigned int incl = tot;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const unsigned int y = __shfl_up_sync(FULL, incl, o);
-                        if (lane >= o) incl += y;
-                    }
-                    const unsigned int total = __shfl_sync(FULL, incl, 31);
-                    if (total == 0u) continue;
-                    if (may_defer && total > a.heavy_cands) {
-                        deferred = true;
-                        break;
-                    }
-                    __syncwarp();
-                    s_end[wib][lane] = incl;
-                    s_beg[wib][lane] = incl - tot;
-                    s_a[wib][lane] = sa;
-                    s_la[wib][lane] = la;
-                    s_b[wib][lane] = sb;
-                    __syncwarp();
-                    // chunks of 32 candidates; the next chunk's rows are loaded
-                    // while the current one is offered to the buffer
-                    constexpr int P = row_floats(D);
-                    auto locate = [&](unsigned int t) -> unsigned int {
-                        return search_pos(s_end[wib], s_beg[wib], s_a[wib], s_la[wib], s_b[wib], t);
-                    };
-                    Row<P> nrow;
-                    unsigned int nrid = 0u;
-                    if (lane < total) {
-                        const unsigned int pos = locate(lane);
-                        nrow.load(a.rows, pos);
-                        nrid = __ldg(a.rid + pos);
-                    }
-                    for (unsigned int cb = 0; cb < total; cb += 32u) {
-                        const unsigned int t = cb + lane;
-                        const Row<P> row = nrow;
-                        const unsigned int rid = nrid;
-                        if (t + 32u < total) {
-                            const unsigned int pos = locate(t + 32u);
-                            nrow.load(a.rows, pos);
-                            nrid = __ldg(a.rid + pos);
-                        }
-                        unsigned long long key = kEmptyKey;
-                        if (t < total) {
-                            float acc = 0.0f;
-#pragma unroll
-                            for (int j = 0; j < D; ++j) {
-                                const float dj = __fsub_rn(s.q[j], row.v[j]);
-                                acc = __fadd_rn(acc, __fmul_rn(dj, dj));
-                            }
-                            if (tk.kth == kEmptyKey ||
-                                acc <= __uint_as_float((unsigned)(tk.kth >> 32)))
-                                key = ((unsigned long long)__float_as_uint(acc) << 32) | rid;
-                        }
-                        updated |= offer(tk, key, lane);
-                    }
-                    __syncwarp();
-                }
-                if (deferred) break;
-            }
-            if (tk.count == tk.k && !updated) break;  // the stop rule of Sec. III.B
-            if (b.covers) break;                      // every occupied cell seen
-            if (a.max_layers > 0 && L - s.lmin + 1 >= a.max_layers) {
-                limited = true;
-                if (lane == 0) atomicOr(a.status, kStatusLimit);
-                break;
-            }
-            ++L;
-        }
-
-        if (deferred) {
+        if (walk_query<D, NS, DENSE>(a, qid, sm[wib], lane, counting, may_defer) && lane == 0) {
             // too much work for one warp: the cooperative kernel takes it
-            if (lane == 0) a.heavy_list[atomicAdd(a.heavy_count, 1u)] = (unsigned int)qid;
-        } else {
-            write_outputs(a, qid, tk, limited, lane);
-            if (counting) {
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    cells += __shfl_xor_sync(FULL, cells, o);
-                    cands += __shfl_xor_sync(FULL, cands, o);
-                }
-                if (lane == 0) {
-                    a.stats[3 * qid + 0] = L + 1;
-                    a.stats[3 * qid + 1] = cells;
-                    a.stats[3 * qid + 2] = cands;
-                }
-            }
+            a.heavy_list[atomicAdd(a.heavy_count, 1u)] = (unsigned int)qid;
         }
         next = __shfl_sync(FULL, next, 0);
     }
@@ -818,190 +829,283 @@ __global__ void __launch_bounds__(kThreads, (MinBlocks<D, NS>::value))
 constexpr int kRoundRows = kThreads;      // rows resolved per round (one per thread)
 constexpr int kRangeCap = 2 * kRoundRows;  // at most two ranges per row
 
-template <int D, int NS, bool DENSE>
-__global__ void __launch_bounds__(kThreads, 1) heavy_kernel(const QueryArgs a)
-{
-    __shared__ unsigned long long s_top[64];
-    __shared__ unsigned long long s_loc[kWarps][64];
-    __shared__ unsigned int r_start[kRangeCap];
-    __shared__ unsigned int r_len[kRangeCap];
-    __shared__ unsigned int r_end[kRangeCap];  // inclusive end of each range, flattened
-    __shared__ unsigned int s_wsum[kWarps];
-    __shared__ unsigned int s_nr, s_h;
-    __shared__ int s_count, s_updated;
+// Shared memory of the cooperative walk.
+struct CoopSmem {
+    unsigned long long top[64];        // the block's buffer
+    unsigned long long loc[kWarps][64];  // each warp's list of the layer
+    unsigned int r_start[kRangeCap];
+    unsigned int r_len[kRangeCap];
+    unsigned int r_end[kRangeCap];  // inclusive end of each range, flattened
+    unsigned int wsum[kWarps];
+    unsigned int nr;
+    int count;
+    int updated;
+};
 
+// One query by the whole block (every thread calls it).
+template <int D, int NS, bool DENSE>
+__device__ __forceinline__ void coop_query(const QueryArgs& a, long long qid, CoopSmem& sm)
+{
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     unsigned long long hmask = 0ull;
     if constexpr (!DENSE) hmask = a.gdev->hmask;
-    const unsigned int nheavy = *a.heavy_count;
+    Query<D> s;
+    query_setup(a, qid, s);
+    if (threadIdx.x < 64) sm.top[threadIdx.x] = kEmptyKey;
+    if (threadIdx.x == 0) sm.count = 0;
+    __syncthreads();
 
+    TopK<NS> tk;
+    long long L = s.lmin;
+    bool limited = false;
     for (;;) {
-        if (threadIdx.x == 0) s_h = atomicAdd(a.heavy_cursor, 1u);
-        __syncthreads();
-        const unsigned int h = s_h;
-        if (h >= nheavy) break;
-        const long long qid = (long long)a.heavy_list[h];
-        Query<D> s;
-        query_setup(a, qid, s);
-        if (threadIdx.x < 64) s_top[threadIdx.x] = kEmptyKey;
-        if (threadIdx.x == 0) s_count = 0;
-        __syncthreads();
-
-        TopK<NS> tk;
-        long long L = s.lmin;
-        bool limited = false;
-        for (;;) {
-            // the block's k-th key at the start of the layer, and an empty
-            // list for this warp's share of the layer
-            const unsigned long long gkth = s_count == a.k ? s_top[a.k - 1] : kEmptyKey;
-            tk.init(a.k);
-            Layer<D> b;
-            const float kd0 = __uint_as_float((unsigned)(gkth >> 32));
-            layer_box(a, s, L, gkth != kEmptyKey && kd0 < 1e30f, kd0, b);
-            if (!b.empty) {
-                const unsigned long long nrows = layer_rows(b);
-                if (nrows >= (1ull << 32)) {
-                    limited = true;
-                    if (threadIdx.x == 0) atomicOr(a.status, kStatusLimit);
-                    break;
-                }
-                RowWalk<D> rw;
-                rw.start(b, (unsigned int)threadIdx.x, (unsigned int)kRoundRows);
-                for (unsigned long long rb = 0; rb < nrows; rb += kRoundRows) {
-                    if (threadIdx.x == 0) s_nr = 0u;
-                    __syncthreads();
-                    unsigned int sa = 0u, la = 0u, sb = 0u, lb = 0u;
-                    long long unused = 0;
-                    const unsigned long long ek = tk.kth < gkth ? tk.kth : gkth;
-                    if (rb + threadIdx.x < nrows)
-                        row_ranges<D, DENSE>(a, hmask, s, b, rw, L, ek != kEmptyKey,
-                                             __uint_as_float((unsigned)(ek >> 32)), false, sa, la,
-                                             sb, lb, unused);
-                    rw.advance(b);
-                    // append the non-empty ranges to the block's list
-                    const unsigned int mine = (la > 0u) + (lb > 0u);
-                    unsigned int incl = mine;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const unsigned int y = __shfl_up_sync(FULL, incl, o);
-                        if (lane >= o) incl += y;
-                    }
-                    unsigned int wbase = 0u;
-                    if (lane == 31 && incl) wbase = atomicAdd(&s_nr, incl);
-                    wbase = __shfl_sync(FULL, wbase, 31);
-                    unsigned int at = wbase + incl - mine;
-                    if (la) {
-                        r_start[at] = sa;
-                        r_len[at] = la;
-                        ++at;
-                    }
-                    if (lb) {
-                        r_start[at] = sb;
-                        r_len[at] = lb;
-                    }
-                    __syncthreads();
-                    // flatten the ranges: inclusive prefix of their lengths
-                    const unsigned int nr = s_nr;
-                    const unsigned int i0 = 2u * threadIdx.x, i1 = i0 + 1u;
-                    const unsigned int v0 = i0 < nr ? r_len[i0] : 0u;
-                    const unsigned int v1 = i1 < nr ? r_len[i1] : 0u;
-                    unsigned int x = v0 + v1;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const unsigned int y = __shfl_up_sync(FULL, x, o);
-                        if (lane >= o) x += y;
-                    }
-                    if (lane == 31) s_wsum[wib] = x;
-                    __syncthreads();
-                    unsigned int pre = 0u;
-                    for (int w2 = 0; w2 < wib; ++w2) pre += s_wsum[w2];
-                    x += pre;
-                    if (i0 < nr) r_end[i0] = x - v1;
-                    if (i1 < nr) r_end[i1] = x;
-                    unsigned int total = 0u;
-                    for (int w2 = 0; w2 < kWarps; ++w2) total += s_wsum[w2];
-                    __syncthreads();
-                    // the candidates, 32 per warp at a time
-                    for (unsigned int cb = 32u * wib; cb < total; cb += 32u * kWarps) {
-                        const unsigned int t = cb + lane;
-                        unsigned long long key = kEmptyKey;
-                        if (t < total) {
-                            unsigned int lo_r = 0u, hi_r = nr - 1u;  // first range ending past t
-                            while (lo_r < hi_r) {
-                                const unsigned int mid = (lo_r + hi_r) >> 1;
-                                if (r_end[mid] > t)
-                                    hi_r = mid;
-                                else
-                                    lo_r = mid + 1u;
-                            }
-                            const unsigned int pos = r_start[lo_r] + (t - (r_end[lo_r] - r_len[lo_r]));
-                            const unsigned long long ek = tk.kth < gkth ? tk.kth : gkth;
-                            key = candidate_key<D>(a, s, pos, ek == kEmptyKey,
-                                                   __uint_as_float((unsigned)(ek >> 32)));
-                        }
-                        offer(tk, key, lane, gkth);
-                    }
-                    __syncthreads();
-                }
-            }
-            // merge the warps' buffers into the block's buffer
-#pragma unroll
-            for (int i = 0; i < NS; ++i) s_loc[wib][i * 32 + lane] = tk.s[i];
-            __syncthreads();
-            if (wib == 0) {
-                // start from the block's buffer; the warps' lists hold only
-                // points of this layer, so the merge has no duplicates
-                TopK<NS> g;
-                g.init(a.k);
-#pragma unroll
-                for (int i = 0; i < NS; ++i) g.s[i] = s_top[i * 32 + lane];
-                g.count = s_count;
-                g.refresh_kth();
-                for (int w2 = 0; w2 < kWarps; ++w2) {
-                    if constexpr (NS == 1) {
-                        g.merge32(s_loc[w2][lane], lane);
-                    } else {
-                        for (int e = 0; e < 64; ++e) {
-                            const unsigned long long xk = s_loc[w2][e];
-                            if (!(xk < g.kth)) break;  // the list is sorted
-                            g.insert(xk, lane);
-                        }
-                    }
-                }
-                bool changed = false;
-#pragma unroll
-                for (int i = 0; i < NS; ++i) changed |= g.s[i] != s_top[i * 32 + lane];
-                changed = __any_sync(FULL, changed);
-                __syncwarp();
-#pragma unroll
-                for (int i = 0; i < NS; ++i) s_top[i * 32 + lane] = g.s[i];
-                if (lane == 0) {
-                    s_count = g.count;
-                    s_updated = changed ? 1 : 0;
-                }
-            }
-            __syncthreads();
-            const bool updated = s_updated != 0;
-            const bool full = s_count == a.k;
-            if (full && !updated) break;  // the stop rule of Sec. III.B
-            if (b.covers) break;
-            if (a.max_layers > 0 && L - s.lmin + 1 >= a.max_layers) {
+        // the block's k-th key at the start of the layer, and an empty list
+        // for this warp's share of the layer
+        const unsigned long long gkth = sm.count == a.k ? sm.top[a.k - 1] : kEmptyKey;
+        tk.init(a.k);
+        Layer<D> b;
+        const float kd0 = __uint_as_float((unsigned)(gkth >> 32));
+        layer_box(a, s, L, gkth != kEmptyKey && kd0 < 1e30f, kd0, b);
+        if (!b.empty) {
+            const unsigned long long nrows = layer_rows(b);
+            if (nrows >= (1ull << 32)) {
                 limited = true;
                 if (threadIdx.x == 0) atomicOr(a.status, kStatusLimit);
                 break;
             }
-            ++L;
+            RowWalk<D> rw;
+            rw.start(b, (unsigned int)threadIdx.x, (unsigned int)kRoundRows);
+            for (unsigned long long rb = 0; rb < nrows; rb += kRoundRows) {
+                if (threadIdx.x == 0) sm.nr = 0u;
+                __syncthreads();
+                unsigned int sa = 0u, la = 0u, sb = 0u, lb = 0u;
+                long long unused = 0;
+                const unsigned long long ek = tk.kth < gkth ? tk.kth : gkth;
+                if (rb + threadIdx.x < nrows)
+                    row_ranges<D, DENSE>(a, hmask, s, b, rw, L, ek != kEmptyKey,
+                                         __uint_as_float((unsigned)(ek >> 32)), false, sa, la, sb,
+                                         lb, unused);
+                rw.advance(b);
+                // append the non-empty ranges to the block's list
+                const unsigned int mine = (la > 0u) + (lb > 0u);
+                unsigned int incl = mine;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned int y = __shfl_up_sync(FULL, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                unsigned int wbase = 0u;
+                if (lane == 31 && incl) wbase = atomicAdd(&sm.nr, incl);
+                wbase = __shfl_sync(FULL, wbase, 31);
+                unsigned int at = wbase + incl - mine;
+                if (la) {
+                    sm.r_start[at] = sa;
+                    sm.r_len[at] = la;
+                    ++at;
+                }
+                if (lb) {
+                    sm.r_start[at] = sb;
+                    sm.r_len[at] = lb;
+                }
+                __syncthreads();
+                // flatten the ranges: inclusive prefix of their lengths
+                const unsigned int nr = sm.nr;
+                const unsigned int i0 = 2u * threadIdx.x, i1 = i0 + 1u;
+                const unsigned int v0 = i0 < nr ? sm.r_len[i0] : 0u;
+                const unsigned int v1 = i1 < nr ? sm.r_len[i1] : 0u;
+                unsigned int x = v0 + v1;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned int y = __shfl_up_sync(FULL, x, o);
+                    if (lane >= o) x += y;
+                }
+                if (lane == 31) sm.wsum[wib] = x;
+                __syncthreads();
+                unsigned int pre = 0u;
+                for (int w2 = 0; w2 < wib; ++w2) pre += sm.wsum[w2];
+                x += pre;
+                if (i0 < nr) sm.r_end[i0] = x - v1;
+                if (i1 < nr) sm.r_end[i1] = x;
+                unsigned int total = 0u;
+                for (int w2 = 0; w2 < kWarps; ++w2) total += sm.wsum[w2];
+                __syncthreads();
+                // the candidates, 32 per warp at a time
+                for (unsigned int cb = 32u * wib; cb < total; cb += 32u * kWarps) {
+                    const unsigned int t = cb + lane;
+                    unsigned long long key = kEmptyKey;
+                    if (t < total) {
+                        unsigned int lo_r = 0u, hi_r = nr - 1u;  // first range ending past t
+                        while (lo_r < hi_r) {
+                            const unsigned int mid = (lo_r + hi_r) >> 1;
+                            if (sm.r_end[mid] > t)
+                                hi_r = mid;
+                            else
+                                lo_r = mid + 1u;
+                        }
+                        const unsigned int pos =
+                            sm.r_start[lo_r] + (t - (sm.r_end[lo_r] - sm.r_len[lo_r]));
+                        const unsigned long long ek2 = tk.kth < gkth ? tk.kth : gkth;
+                        key = candidate_key<D>(a, s, pos, ek2 == kEmptyKey,
+                                               __uint_as_float((unsigned)(ek2 >> 32)));
+                    }
+                    offer(tk, key, lane, gkth);
+                }
+                __syncthreads();
+            }
         }
+        // merge the warps' lists into the block's buffer
+#pragma unroll
+        for (int i = 0; i < NS; ++i) sm.loc[wib][i * 32 + lane] = tk.s[i];
+        __syncthreads();
         if (wib == 0) {
+            // start from the block's buffer; the warps' lists hold only points
+            // of this layer, so the merge has no duplicates
             TopK<NS> g;
             g.init(a.k);
 #pragma unroll
-            for (int i = 0; i < NS; ++i) g.s[i] = s_top[i * 32 + lane];
-            g.count = s_count;
-            write_outputs(a, qid, g, limited, lane);
+            for (int i = 0; i < NS; ++i) g.s[i] = sm.top[i * 32 + lane];
+            g.count = sm.count;
+            g.refresh_kth();
+            for (int w2 = 0; w2 < kWarps; ++w2) {
+                if constexpr (NS == 1) {
+                    g.merge32(sm.loc[w2][lane], lane);
+                } else {
+                    for (int e = 0; e < 64; ++e) {
+                        const unsigned long long xk = sm.loc[w2][e];
+                        if (!(xk < g.kth)) break;  // the list is sorted
+                        g.insert(xk, lane);
+                    }
+                }
+            }
+            bool changed = false;
+#pragma unroll
+            for (int i = 0; i < NS; ++i) changed |= g.s[i] != sm.top[i * 32 + lane];
+            changed = __any_sync(FULL, changed);
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < NS; ++i) sm.top[i * 32 + lane] = g.s[i];
+            if (lane == 0) {
+                sm.count = g.count;
+                sm.updated = changed ? 1 : 0;
+            }
         }
         __syncthreads();
+        const bool updated = sm.updated != 0;
+        const bool full = sm.count == a.k;
+        if (full && !updated) break;  // the stop rule of Sec. III.B
+        if (b.covers) break;
+        if (a.max_layers > 0 && L - s.lmin + 1 >= a.max_layers) {
+            limited = true;
+            if (threadIdx.x == 0) atomicOr(a.status, kStatusLimit);
+            break;
+        }
+        ++L;
+    }
+    if (wib == 0) {
+        TopK<NS> g;
+        g.init(a.k);
+#pragma unroll
+        for (int i = 0; i < NS; ++i) g.s[i] = sm.top[i * 32 + lane];
+        g.count = sm.count;
+        write_outputs(a, qid, g, limited, lane);
+    }
+    __syncthreads();
+}
+
+template <int D, int NS, bool DENSE>
+__global__ void __launch_bounds__(kThreads, 1) heavy_kernel(const QueryArgs a)
+{
+    __shared__ CoopSmem sm;
+    __shared__ unsigned int s_h;
+    const unsigned int nheavy = *a.heavy_count;
+    for (;;) {
+        if (threadIdx.x == 0) s_h = atomicAdd(a.heavy_cursor, 1u);
+        __syncthreads();
+        const unsigned int h = s_h;
+        __syncthreads();
+        if (h >= nheavy) break;
+        coop_query<D, NS, DENSE>(a, (long long)a.heavy_list[h], sm);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Batched indexes: one persistent launch per dimension covers the queries of
+// every index of that dimension.  Each query finds its index by binary search
+// over the group's query offsets and runs the same walk with that index's
+// arguments (read through L1 from the group's argument array).
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int group_index(const unsigned long long* qoff, int count,
+                                           unsigned long long qi)
+{
+    int lo = 0, hi = count - 1;  // the last index whose first query is <= qi
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(qoff + mid) <= qi)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int D>
+__global__ void __launch_bounds__(kThreads, (MinBlocks<D, 1>::value))
+    batch_query_kernel(const BatchArgs g)
+{
+    __shared__ WarpSmem sm[kWarps];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const bool may_defer = g.heavy_list != nullptr;
+    unsigned long long next = 0ull;
+    if (lane == 0) next = atomicAdd(g.counter, 1ull);
+    next = __shfl_sync(FULL, next, 0);
+    while (next < g.total) {
+        const unsigned long long qi = next;
+        if (lane == 0) next = atomicAdd(g.counter, 1ull);
+        const int i = group_index(g.qoff, g.count, qi);
+        const QueryArgs& a = g.args[i];
+        const long long qid = (long long)(qi - __ldg(g.qoff + i));
+        bool deferred;
+        if (a.k <= 32)
+            deferred = a.dense ? walk_query<D, 1, true>(a, qid, sm[wib], lane, false, may_defer)
+                               : walk_query<D, 1, false>(a, qid, sm[wib], lane, false, may_defer);
+        else
+            deferred = a.dense ? walk_query<D, 2, true>(a, qid, sm[wib], lane, false, may_defer)
+                               : walk_query<D, 2, false>(a, qid, sm[wib], lane, false, may_defer);
+        if (deferred && lane == 0) g.heavy_list[atomicAdd(g.heavy_count, 1u)] = (unsigned int)qi;
+        next = __shfl_sync(FULL, next, 0);
+    }
+}
+
+template <int D>
+__global__ void __launch_bounds__(kThreads, 1) batch_heavy_kernel(const BatchArgs g)
+{
+    __shared__ CoopSmem sm;
+    __shared__ unsigned int s_h;
+    const unsigned int nheavy = *g.heavy_count;
+    for (;;) {
+        if (threadIdx.x == 0) s_h = atomicAdd(g.heavy_cursor, 1u);
+        __syncthreads();
+        const unsigned int h = s_h;
+        __syncthreads();
+        if (h >= nheavy) break;
+        const unsigned long long qi = g.heavy_list[h];
+        const int i = group_index(g.qoff, g.count, qi);
+        const QueryArgs& a = g.args[i];
+        const long long qid = (long long)(qi - __ldg(g.qoff + i));
+        if (a.k <= 32) {
+            if (a.dense)
+                coop_query<D, 1, true>(a, qid, sm);
+            else
+                coop_query<D, 1, false>(a, qid, sm);
+        } else {
+            if (a.dense)
+                coop_query<D, 2, true>(a, qid, sm);
+            else
+                coop_query<D, 2, false>(a, qid, sm);
+        }
     }
 }
 
@@ -1033,6 +1137,25 @@ cudaError_t launch_one(const QueryArgs& a, int sms, cudaStream_t s)
     if (hb > a.m) hb = a.m;
     if (hb < 1) hb = 1;
     heavy_kernel<D, NS, DENSE><<<(int)hb, kThreads, 0, s>>>(a);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t launch_batch_d(const BatchArgs& g, int sms, cudaStream_t s)
+{
+    static int per_sm = 0, per_sm_heavy = 0;
+    long long blocks = (long long)sms * blocks_per_sm(batch_query_kernel<D>, per_sm);
+    const long long need = (long long)((g.total + kWarps - 1) / kWarps);
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    batch_query_kernel<D><<<(int)blocks, kThreads, 0, s>>>(g);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || g.heavy_list == nullptr) return e;
+    long long hb = (long long)sms * blocks_per_sm(batch_heavy_kernel<D>, per_sm_heavy);
+    if (hb > (long long)g.total) hb = (long long)g.total;
+    if (hb < 1) hb = 1;
+    batch_heavy_kernel<D><<<(int)hb, kThreads, 0, s>>>(g);
     count_launches(1);
     return cudaGetLastError();
 }

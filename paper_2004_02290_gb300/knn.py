@@ -39,7 +39,9 @@ class knn_index_info_t(ctypes.Structure):
                 ("has_labels", ctypes.c_int32)]
 
 
-EXPORTED = ["knn_build", "knn_query", "knn_query_stats", "knn_query_noalloc", "knn_index_info",
+EXPORTED = ["knn_batch_build", "knn_batch_info", "knn_batch_query", "knn_batch_plan",
+            "knn_batch_run", "knn_plan_free", "knn_batch_free",
+            "knn_build", "knn_query", "knn_query_stats", "knn_query_noalloc", "knn_index_info",
             "knn_index_export",
             "knn_timing_enable", "knn_timing_read", "knn_kernel_launches", "knn_free",
             "knn_last_error", "knn_abi_version"]
@@ -82,6 +84,25 @@ def library(path: str | None = None) -> ctypes.CDLL:
         lib.knn_timing_read.restype = i32
         lib.knn_kernel_launches.argtypes = []
         lib.knn_kernel_launches.restype = i64
+        pp = ctypes.POINTER(vp)
+        lib.knn_batch_build.argtypes = [i32, pp, pp, ctypes.POINTER(i64), ctypes.POINTER(i32),
+                                        ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i32), vp,
+                                        ctypes.POINTER(vp)]
+        lib.knn_batch_build.restype = i32
+        lib.knn_batch_info.argtypes = [vp, i32, ctypes.POINTER(knn_index_info_t)]
+        lib.knn_batch_info.restype = i32
+        lib.knn_batch_query.argtypes = [vp, pp, ctypes.POINTER(i64), ctypes.POINTER(i32),
+                                        ctypes.POINTER(i32), pp, pp, pp, i32, vp]
+        lib.knn_batch_query.restype = i32
+        lib.knn_batch_plan.argtypes = [vp, pp, ctypes.POINTER(i64), ctypes.POINTER(i32),
+                                       ctypes.POINTER(i32), pp, pp, pp, ctypes.POINTER(vp)]
+        lib.knn_batch_plan.restype = i32
+        lib.knn_batch_run.argtypes = [vp, i32, vp]
+        lib.knn_batch_run.restype = i32
+        lib.knn_plan_free.argtypes = [vp]
+        lib.knn_plan_free.restype = None
+        lib.knn_batch_free.argtypes = [vp]
+        lib.knn_batch_free.restype = None
         _lib = lib
         return lib
 
@@ -252,6 +273,126 @@ def knn_query_noalloc(index: Index, queries, k: int, mode: int, ids, dist2=None,
                                        _stream(stream, queries, ids)))
     del kq, ki, kd, kp
     return ids, dist2, pred
+
+
+def _ptr_array(items):
+    """A ctypes array of the addresses of tensors (None -> NULL) and their keepalives."""
+    arr = (ctypes.c_void_p * len(items))()
+    keep = []
+    for i, a in enumerate(items):
+        p, k = _ptr(a)
+        arr[i] = p
+        keep.append(k)
+    return arr, keep
+
+
+class Batch:
+    """A batch of independent indexes built in one pass (knn_batch_build)."""
+
+    def __init__(self, handle, ns, ds):
+        self._h = handle
+        self.ns = list(ns)
+        self.ds = list(ds)
+        self.count = len(self.ns)
+
+    def info(self, i: int) -> knn_index_info_t:
+        out = knn_index_info_t()
+        _check(library().knn_batch_info(self._h, i, ctypes.byref(out)))
+        return out
+
+    def _outputs(self, queries, ks, modes):
+        ids, d2, pred = [], [], []
+        for q, k, mode in zip(queries, ks, modes):
+            m = int(q.shape[0])
+            ids.append(_alloc_like(q, (m, k), "int32"))
+            d2.append(_alloc_like(q, (m, k), "float32"))
+            pred.append(None if mode < 0 else
+                        _alloc_like(q, (m,), "int32" if mode == KNN_VOTE else "float32"))
+        return ids, d2, pred
+
+    def _arrays(self, queries, ks, modes, ids, d2, pred):
+        if not (len(queries) == len(ks) == len(modes) == self.count):
+            raise ValueError("one query set, k and mode per index")
+        m = (ctypes.c_int64 * self.count)(*[int(q.shape[0]) for q in queries])
+        k = (ctypes.c_int32 * self.count)(*ks)
+        md = (ctypes.c_int32 * self.count)(*modes)
+        qa, kq = _ptr_array(queries)
+        ia, ki = _ptr_array(ids)
+        da, kd = _ptr_array(d2)
+        pa, kp = _ptr_array(pred)
+        return (m, k, md, qa, ia, da, pa), (kq, ki, kd, kp)
+
+    def query(self, queries, ks, modes, flags: int = 0, stream=None):
+        """Query every index; returns lists (ids, dist2, pred) with one entry per index."""
+        ids, d2, pred = self._outputs(queries, ks, modes)
+        (m, k, md, qa, ia, da, pa), keep = self._arrays(queries, ks, modes, ids, d2, pred)
+        _check(library().knn_batch_query(self._h, qa, m, k, md, ia, da, pa, flags,
+                                         _stream(stream, *queries)))
+        del keep
+        return ids, d2, pred
+
+    def plan(self, queries, ks, modes):
+        """Capture the query of these buffers in a CUDA graph; returns (Plan, ids, dist2, pred)."""
+        ids, d2, pred = self._outputs(queries, ks, modes)
+        (m, k, md, qa, ia, da, pa), keep = self._arrays(queries, ks, modes, ids, d2, pred)
+        h = ctypes.c_void_p()
+        _check(library().knn_batch_plan(self._h, qa, m, k, md, ia, da, pa, ctypes.byref(h)))
+        return Plan(h, (queries, ids, d2, pred, keep)), ids, d2, pred
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            library().knn_batch_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Plan:
+    """A batch query captured in a CUDA graph (knn_batch_plan); run() replays it."""
+
+    def __init__(self, handle, keep):
+        self._h = handle
+        self._keep = keep  # the buffers the graph reads and writes
+
+    def run(self, flags: int = 0, stream=None):
+        _check(library().knn_batch_run(self._h, flags, _stream(stream, *self._keep[0])))
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            library().knn_plan_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def knn_batch_build(points, labels, widths, tables=None, stream=None) -> Batch:
+    """Build one index per entry of `points` (lists; labels entries may be None)."""
+    count = len(points)
+    for p in points:
+        if p.ndim != 2:
+            raise ValueError("points must be n x d")
+        _check_f32(p, "points")
+    ns = [int(p.shape[0]) for p in points]
+    ds = [int(p.shape[1]) for p in points]
+    pa, kp = _ptr_array(points)
+    la, kl = _ptr_array(labels if labels is not None else [None] * count)
+    n = (ctypes.c_int64 * count)(*ns)
+    d = (ctypes.c_int32 * count)(*ds)
+    w = (ctypes.c_float * count)(*[float(np.float32(x)) for x in widths])
+    t = None if tables is None else (ctypes.c_int32 * count)(*tables)
+    h = ctypes.c_void_p()
+    _check(library().knn_batch_build(count, pa, la, n, d, w, t, _stream(stream, *points),
+                                     ctypes.byref(h)))
+    del kp, kl
+    return Batch(h, ns, ds)
 
 
 def knn_free(index: Index):

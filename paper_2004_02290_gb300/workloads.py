@@ -194,3 +194,39 @@ def regression_targets(points, seed):
     p = points.astype(np.float64)
     y = np.sin(3.0 * p[:, 0]) + 0.5 * p.sum(axis=1) + 0.01 * rng.standard_normal(p.shape[0])
     return y.astype(np.float32)
+
+
+def gen_batched(count=256, seed=3, n_lo=1_000, n_hi=2_000_000, dims=(2, 3, 4, 6),
+                ks=(1, 5, 15, 32)):
+    """Many independent problems of uneven size, for the batched form.
+
+    Per problem: n log-uniform in [n_lo, n_hi], d uniform in `dims`, k uniform
+    in `ks`, m = n // 10 queries (at least 1) from the same mixture; points
+    from a Gaussian mixture with 4..32 clusters (centres uniform in [0,1]^d,
+    sigma uniform in [0.02, 0.1]).  Even problems are classification (label =
+    cluster), odd ones regression (a smooth target plus noise).  Cell widths
+    are left unset (w = nan): the autotuner chooses them.
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(round(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi)))))
+        d = int(rng.choice(dims))
+        k = int(rng.choice(ks))
+        m = max(1, n // 10)
+        ncl = int(rng.integers(4, 33))
+        sigma = float(rng.uniform(0.02, 0.1))
+        centres = rng.random((ncl, d))
+        comp = rng.integers(0, ncl, size=n)
+        x = _f32(centres[comp] + sigma * rng.standard_normal((n, d)))
+        qc = rng.integers(0, ncl, size=m)
+        q = _f32(centres[qc] + sigma * rng.standard_normal((m, d)))
+        if i % 2 == 0:
+            mode, lab = VOTE, comp.astype(np.int32)
+        else:
+            xd = x.astype(np.float64)
+            y = np.sin(3.0 * xd[:, 0]) + 0.5 * xd.sum(axis=1) + 0.05 * rng.standard_normal(n)
+            mode, lab = MEAN, y.astype(np.float32)
+        out.append(Workload(name=f"batched[{i}]", points=x, labels=lab, queries=q, k=k,
+                            mode=mode, w=float("nan"), table=TABLE_AUTO, seed=seed))
+    return out

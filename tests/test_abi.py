@@ -108,3 +108,21 @@ def test_binding_refuses_missing_library(tmp_path):
             knn.library(str(tmp_path / "missing.so"))
     finally:
         knn._lib = saved
+
+
+def test_batch_build_rejects_bad_arguments(lib):
+    h = ctypes.c_void_p()
+    n = (ctypes.c_int64 * 1)(10)
+    d = (ctypes.c_int32 * 1)(2)
+    w = (ctypes.c_float * 1)(1.0)
+    pts = (ctypes.c_void_p * 1)(None)
+    assert lib.knn_batch_build(0, pts, None, n, d, w, None, None, ctypes.byref(h)) == knn.KNN_EINVAL
+    bad_d = (ctypes.c_int32 * 1)(9)
+    assert lib.knn_batch_build(1, pts, None, n, bad_d, w, None, None,
+                               ctypes.byref(h)) == knn.KNN_EINVAL
+    bad_w = (ctypes.c_float * 1)(-1.0)
+    assert lib.knn_batch_build(1, pts, None, n, d, bad_w, None, None,
+                               ctypes.byref(h)) == knn.KNN_EINVAL
+    assert not h.value
+    lib.knn_batch_free(None)
+    lib.knn_plan_free(None)
