@@ -49,7 +49,9 @@ def parse_args(argv=None):
     p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--config", default="large_cls", choices=list(wl.SPECS))
+    p.add_argument("--config", default="large_cls", choices=list(wl.SPECS) + ["batched"])
+    p.add_argument("--batch-count", type=int, default=256,
+                   help="problems of the batched workload")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=50_000,
@@ -429,10 +431,116 @@ def run_e2e(w, knn, dev, args):
             "d2h_bytes_per_step": int(d2h), "ms_per_step": sec * 1e3}
 
 
+def run_batched(args):
+    """Batched form against plain form on many uneven problems (one GPU).
+
+    Both forms rebuild every index and answer every query each step; the
+    batched step is knn_batch_build + knn_batch_query, the plain step is
+    knn_build + knn_query per problem.  Widths come from the autotuner
+    (untimed).  Outputs of the two forms are compared element by element.
+    """
+    import torch
+
+    import __graft_entry__
+    from paper_2004_02290_gb300 import autotune, knn
+
+    __graft_entry__.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    ps = wl.gen_batched(args.batch_count, seed=3)
+    widths, tune_s, _ = autotune.tune_batch(ps, dev=dev)
+    for p_, w_ in zip(ps, widths):
+        p_.w = w_
+    pts = [torch.from_numpy(p_.points).to(dev) for p_ in ps]
+    lab = [torch.from_numpy(p_.labels).to(dev) for p_ in ps]
+    qs = [torch.from_numpy(p_.queries).to(dev) for p_ in ps]
+    ks = [p_.k for p_ in ps]
+    modes = [p_.mode for p_ in ps]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    plain_out = [(torch.empty((p_.m, p_.k), dtype=torch.int32, device=dev),
+                  torch.empty((p_.m, p_.k), dtype=torch.float32, device=dev),
+                  torch.empty(p_.m, dtype=torch.int32 if p_.mode == wl.VOTE else torch.float32,
+                              device=dev)) for p_ in ps]
+
+    def plain_step():
+        for i, p_ in enumerate(ps):
+            idx = knn.knn_build(pts[i], lab[i], p_.w)
+            knn.knn_query(idx, qs[i], p_.k, p_.mode, ids=plain_out[i][0], dist2=plain_out[i][1],
+                          pred=plain_out[i][2])
+            idx.free()
+
+    def batched_step():
+        b = knn.knn_batch_build(pts, lab, widths)
+        out = b.query(qs, ks, modes)
+        b.free()
+        return out
+
+    def timed(fn, steps):
+        ms = []
+        out = None
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms, out
+
+    for _ in range(args.warmup):
+        plain_step()
+        batched_step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    l0 = knn.knn_kernel_launches()
+    b_ms, bout = timed(batched_step, args.steps)
+    lb = knn.knn_kernel_launches() - l0
+    p_ms, _ = timed(plain_step, args.steps)
+    clocks = sampler.stop()
+    # the query alone: direct launches and a replayed CUDA graph on a built batch
+    batch = knn.knn_batch_build(pts, lab, widths)
+    q_ms, _ = timed(lambda: batch.query(qs, ks, modes), args.steps)
+    plan, gi, gd, gp = batch.plan(qs, ks, modes)
+    g_ms, _ = timed(lambda: plan.run(), args.steps)
+    torch.cuda.synchronize()
+    identical = all(torch.equal(bout[0][i], plain_out[i][0]) and
+                    torch.equal(bout[1][i], plain_out[i][1]) and
+                    torch.equal(bout[2][i].view(torch.int32), plain_out[i][2].view(torch.int32))
+                    for i in range(len(ps)))
+    graph_identical = all(torch.equal(gi[i], bout[0][i]) for i in range(len(ps)))
+    plan.free()
+    batch.free()
+    total_q = sum(p_.m for p_ in ps)
+    b_step = float(np.mean(b_ms))
+    p_step = float(np.mean(p_ms))
+    print(json.dumps({
+        "metric": "queries/sec, batched vs plain grid-KNN (build + query per step)",
+        "value": total_q / (b_step * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": b_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batched", "problems": len(ps),
+                   "points": int(sum(p_.n for p_ in ps)), "queries": int(total_q),
+                   "dims": sorted({p_.d for p_ in ps}), "ks": sorted({p_.k for p_ in ps}),
+                   "l2": "flushed before every step (512 MiB write)",
+                   "widths": "autotuned per problem (untimed, %.1f s)" % tune_s},
+        "plain": {"value": total_q / (p_step * 1e-3), "ms_per_step": p_step},
+        "speedup_vs_plain": p_step / b_step,
+        "query_only_ms": {"direct": float(np.mean(q_ms)), "graph_replay": float(np.mean(g_ms))},
+        "identical_to_plain": bool(identical), "graph_identical": bool(graph_identical),
+        "gpu_launches_batched": int(lb), "clocks": clocks,
+    }), flush=True)
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 

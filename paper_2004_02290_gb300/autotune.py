@@ -2,9 +2,10 @@
 
 The paper measures cells from the data (Sec. III.A); the library takes the
 width from the caller.  For a problem set, the tuner picks each index's width
-by measurement on the GPU: for a few candidate widths around a starting guess
-it builds the index and times a sample of the queries, and keeps the width of
-the least estimated time (build + sampled query time scaled to all queries).
+by measurement on the GPU: starting from a guess, it walks a grid of widths
+(half powers of two) downhill, building the index and timing a sample of the
+queries at each, and keeps the width of the least estimated time (build +
+sampled query time scaled to all queries).
 The kernels' tile shape (one warp per query, 32-candidate chunks, the
 number of resident blocks) is fixed by the design and its occupancy sweep.
 
@@ -38,9 +39,32 @@ def start_width(points: np.ndarray, k: int) -> float:
     return float(np.float32((vol * occ / n) ** (1.0 / d)))
 
 
-def tune_width(points, labels, queries, k: int, mode: int, factors=(0.5, 0.71, 1.0, 1.41, 2.0),
-               sample: int = 4096, dev=None) -> Choice:
-    """Width of least estimated build + query time for one problem (GPU)."""
+def _estimate(pts, lab, q, k, mode, m, s, w, stream):
+    """Build + sampled query time (ms) at width w, query time scaled to m; None if unbuildable."""
+    import torch
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    try:
+        ev[0].record(stream)
+        idx = knn.knn_build(pts, lab, w)
+        ev[1].record(stream)
+        idx.query(q, k, mode if lab is not None else knn.KNN_NONE)
+        ev[2].record(stream)
+        ev[2].synchronize()
+        idx.free()
+    except knn.KnnError:
+        return None  # a width the index cannot hold (grid too fine)
+    return ev[0].elapsed_time(ev[1]) + ev[1].elapsed_time(ev[2]) * (m / s)
+
+
+def tune_width(points, labels, queries, k: int, mode: int, step: float = 0.5,
+               max_steps: int = 10, sample: int = 4096, dev=None) -> Choice:
+    """Width of least estimated build + query time for one problem (GPU).
+
+    Walks downhill on a grid of widths w0 * 2^(step * i) from the starting
+    guess w0, one step at a time, until the cost rises (at most max_steps
+    steps each way).
+    """
     import torch
 
     dev = dev or torch.device("cuda:0")
@@ -53,34 +77,37 @@ def tune_width(points, labels, queries, k: int, mode: int, factors=(0.5, 0.71, 1
     rng = np.random.default_rng(0)
     pick = np.sort(rng.choice(m, size=s, replace=False)) if s < m else np.arange(m)
     q = torch.from_numpy(np.ascontiguousarray(queries[pick], np.float32)).to(dev)
-    tried = []
-    best = None
     stream = torch.cuda.current_stream(dev)
-    for f in factors:
-        w = float(np.float32(w0 * f))
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        try:
-            ev[0].record(stream)
-            idx = knn.knn_build(pts, lab, w)
-            ev[1].record(stream)
-            idx.query(q, k, mode if lab is not None else knn.KNN_NONE)
-            ev[2].record(stream)
-            ev[2].synchronize()
-            idx.free()
-        except knn.KnnError:
-            continue  # a width the index cannot hold (grid too fine)
-        est = ev[0].elapsed_time(ev[1]) + ev[1].elapsed_time(ev[2]) * (m / s)
-        tried.append((w, est))
-        if best is None or est < best[1]:
-            best = (w, est)
-    if best is None:
+    cache = {}
+
+    def cost(i):
+        if i not in cache:
+            w = float(np.float32(w0 * 2.0 ** (step * i)))
+            cache[i] = (w, _estimate(pts, lab, q, k, mode, m, s, w, stream))
+        return cache[i][1]
+
+    i = 0
+    c0 = cost(0)
+    if c0 is None:
+        i, c0 = 1, cost(1)
+    for direction in (-1, 1):
+        j = i
+        for _ in range(max_steps):
+            c = cost(j + direction)
+            if c is None or c0 is None or c >= c0:
+                break
+            j += direction
+            c0 = c
+        i = j
+    tried = sorted((w, c) for w, c in cache.values() if c is not None)
+    if not tried:
         raise RuntimeError("no candidate width could be built")
+    best = min(tried, key=lambda t: t[1])
     return Choice(width=best[0], est_ms=best[1], tried=tried)
 
 
-def tune_batch(problems, dev=None, factors=(0.5, 0.71, 1.0, 1.41, 2.0)):
+def tune_batch(problems, dev=None):
     """Widths for every problem; returns (widths, seconds spent, choices)."""
     t0 = time.perf_counter()
-    choices = [tune_width(p.points, p.labels, p.queries, p.k, p.mode, factors=factors, dev=dev)
-               for p in problems]
+    choices = [tune_width(p.points, p.labels, p.queries, p.k, p.mode, dev=dev) for p in problems]
     return [c.width for c in choices], time.perf_counter() - t0, choices

@@ -725,7 +725,7 @@ knn_status batch_build_impl(int count, const float* const* points, const void* c
             a.key_prefix = (unsigned long long)i << shift;
             a.gdev = b->gdev;
             a.max_layers = max_layers_default();
-            a.heavy_rows = heavy_rows_default();
+            a.heavy_rows = heavy_rows_default(ds.d);
             a.heavy_cands = heavy_cands_default();
         }
     }

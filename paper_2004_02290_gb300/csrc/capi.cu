@@ -88,15 +88,18 @@ unsigned int env_uint(const char* name, unsigned int dflt)
     return v <= 0 ? 0xffffffffu : (unsigned int)(v > 0xffffffffll ? 0xffffffffll : v);
 }
 
-unsigned int heavy_rows_env()
+// Defaults measured on GB300: a layer of more than 1024 rows (d <= 4) or 4096
+// rows (d >= 5), or a row batch of more than 8192 candidates.
+unsigned int heavy_rows_env(int d)
 {
-    static unsigned int v = env_uint("GHN_HEAVY_ROWS", 1024u);
-    return v;
+    static unsigned int v = env_uint("GHN_HEAVY_ROWS", 0u);  // 0: unset
+    if (v != 0u) return v;  // a value, or all ones (no deferral) for a value <= 0
+    return d <= 4 ? 1024u : 4096u;
 }
 
 unsigned int heavy_cands_env()
 {
-    static unsigned int v = env_uint("GHN_HEAVY_CANDS", 2048u);
+    static unsigned int v = env_uint("GHN_HEAVY_CANDS", 8192u);
     return v;
 }
 
@@ -561,7 +564,7 @@ knn_status query_impl(const ghn_index* x, const float* queries_user, long long m
         a.heavy_count = reinterpret_cast<unsigned int*>(scratch + 2);
         a.heavy_cursor = reinterpret_cast<unsigned int*>(scratch + 2) + 1;
         a.heavy_list = heavy;
-        a.heavy_rows = heavy_rows_env();
+        a.heavy_rows = heavy_rows_env(x->d);
         a.heavy_cands = heavy_cands_env();
         a.stats = stats;
         a.order = order;
@@ -660,7 +663,7 @@ void index_query_args(const ghn_index* x, QueryArgs& a)
     a.bitmap = x->bitmap;
     a.gdev = x->gdev;
     a.max_layers = max_layers_env();
-    a.heavy_rows = heavy_rows_env();
+    a.heavy_rows = heavy_rows_env(x->d);
     a.heavy_cands = heavy_cands_env();
     a.dense = x->table == KNN_TABLE_DENSE;
 }
@@ -689,7 +692,7 @@ void device_free(void* p, cudaStream_t s)
     if (p) cudaFreeAsync(p, s);
 }
 
-unsigned int heavy_rows_default() { return heavy_rows_env(); }
+unsigned int heavy_rows_default(int d) { return heavy_rows_env(d); }
 unsigned int heavy_cands_default() { return heavy_cands_env(); }
 long long max_layers_default() { return max_layers_env(); }
 void tune_device_pool(int dev) { tune_pool(dev); }

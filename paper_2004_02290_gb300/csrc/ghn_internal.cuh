@@ -182,7 +182,7 @@ void index_mark_use(const ghn_index* x, cudaStream_t s);
 // Allocation through the library's pool (with the GHN_FAIL_ALLOC_AT injector).
 int device_alloc(void** p, size_t bytes, cudaStream_t s, const char* what);
 void device_free(void* p, cudaStream_t s);
-unsigned int heavy_rows_default();
+unsigned int heavy_rows_default(int d);
 unsigned int heavy_cands_default();
 long long max_layers_default();
 void tune_device_pool(int dev);

@@ -644,10 +644,11 @@ __device__ __forceinline__ unsigned int search_pos(const unsigned int* end, cons
 
 // Resident blocks per SM the warp kernel is compiled for.  The walk is bound by
 // memory latency, so more resident warps pay even when the register cap
-// spills a little to L1 (measured on the d=3 and d=4 workloads).
+// spills a little to L1 (measured on the d=3 and d=4 workloads; for d >= 5
+// four blocks fit without spills and more gave nothing).
 template <int D, int NS>
 struct MinBlocks {
-    static constexpr int value = (D <= 4 && NS == 1) ? 8 : 2;
+    static constexpr int value = NS == 1 ? (D <= 4 ? 8 : 4) : 2;
 };
 
 // Per-warp shared memory of the walk: the lanes' ranges of one row batch.
