@@ -43,6 +43,10 @@
  *   vote      largest count, ties to the smallest label.
  *   mean      double-precision sum in neighbour order divided by the count,
  *             rounded to single precision.
+ *   median    (Sec. I and Sec. III.D name the median beside the average) the
+ *             outputs sorted by IEEE total order (-0 before +0); an odd count
+ *             takes the middle one, an even count the two middle ones a <= b
+ *             as (double(a) + double(b)) / 2 rounded to single precision.
  */
 #include <math.h>
 #include <stdint.h>
@@ -369,11 +373,43 @@ static int visit_cell(const int64_t* c, void* vctx)
     return 0;
 }
 
+/* IEEE total-order key of a float: unsigned comparison of keys orders
+   -NaN < -inf < ... < -0 < +0 < ... < +inf < +NaN. */
+static uint32_t total_order_key(float v)
+{
+    uint32_t u;
+    memcpy(&u, &v, sizeof u);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+static int cmp_total_order(const void* a, const void* b)
+{
+    uint32_t x = total_order_key(*(const float*)a), y = total_order_key(*(const float*)b);
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+/* Median of the outputs of the first `size` buffer entries (NaN when empty). */
+static float median_of(const ghn_oracle* g, const oracle_entry* buf, int32_t size)
+{
+    if (size == 0) return NAN;
+    float* v = (float*)malloc(sizeof(float) * (size_t)size);
+    if (!v) return NAN;
+    for (int32_t r = 0; r < size; ++r) memcpy(&v[r], &g->labels[buf[r].id], sizeof(float));
+    qsort(v, (size_t)size, sizeof(float), cmp_total_order);
+    float out;
+    if (size % 2)
+        out = v[size / 2];
+    else
+        out = (float)(((double)v[size / 2 - 1] + (double)v[size / 2]) / 2.0);
+    free(v);
+    return out;
+}
+
 /*
  * Predict one query.  ids[k] / dist2[k] receive the neighbours in
  * (distance, index) order, padded with -1 / +inf.  mode 0 = vote (labels read
- * as int32, pred is int32), mode 1 = mean (labels read as float, pred is
- * float), mode -1 = no prediction.  stats (may be NULL) receives
+ * as int32, pred is int32), mode 1 = mean and mode 2 = median (labels read as
+ * float, pred is float), mode -1 = no prediction.  stats (may be NULL) receives
  * {layers visited (L* + 1), occupied cells looked up, points examined}.
  * stop_rule = 0 disables the paper's stop rule (the walk then ends only when
  * the cube covers the box: exhaustive search), for tests.
@@ -382,7 +418,7 @@ static int visit_cell(const int64_t* c, void* vctx)
 int oracle_query_ex(const ghn_oracle* g, const float* q, int32_t k, int32_t mode, int32_t stop_rule,
                     int32_t* ids, float* dist2, void* pred, int64_t* stats)
 {
-    if (!g || k < 1 || (mode >= 0 && !g->labels) || mode > 1) return 1;
+    if (!g || k < 1 || (mode >= 0 && !g->labels) || mode > 2) return 1;
     for (int32_t j = 0; j < g->d; ++j)
         if (!isfinite(q[j])) return 1;
     int32_t d = g->d;
@@ -450,6 +486,8 @@ int oracle_query_ex(const ghn_oracle* g, const float* q, int32_t k, int32_t mode
             sum += (double)y;
         }
         *(float*)pred = x.size ? (float)(sum / (double)x.size) : NAN;
+    } else if (mode == 2) {
+        *(float*)pred = median_of(g, buf, x.size);
     }
     if (stats) {
         stats[0] = L + 1;

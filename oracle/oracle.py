@@ -161,7 +161,7 @@ class Grid:
     def query(self, queries, k: int, mode: int = -1, stats: bool = False):
         """Neighbours of each query: (ids m x k, dist2 m x k, pred m or None[, stats m x 3]).
 
-        mode: 0 vote (int32 outputs), 1 mean (float outputs), -1 none.
+        mode: 0 vote (int32 outputs), 1 mean, 2 median (float outputs), -1 none.
         """
         q = _f32(queries).reshape(-1, self.d)
         m = q.shape[0]
@@ -170,7 +170,7 @@ class Grid:
         pred = None
         if mode == 0:
             pred = np.zeros(m, np.int32)
-        elif mode == 1:
+        elif mode in (1, 2):
             pred = np.zeros(m, np.float32)
         st = np.zeros((m, 3), np.int64) if stats else None
         rc = self._lib.oracle_query(self._h, _ptr(q, _f32p), m, k, mode, _ptr(ids, _i32p),

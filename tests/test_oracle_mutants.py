@@ -53,6 +53,12 @@ MUTANTS = [
      "if (t > GHN_ORACLE_QCLAMP) t = -GHN_ORACLE_QCLAMP;"),
     ("hash_match_always", "if (same_coords(g->cells[e].c, c, g->d)) return e;", "return e;"),
     ("layers_count", "stats[0] = L + 1;", "stats[0] = L;"),
+    ("median_upper_middle", "out = (float)(((double)v[size / 2 - 1] + (double)v[size / 2]) / 2.0);",
+     "out = v[size / 2];"),
+    ("median_natural_order", "return x < y ? -1 : (x > y ? 1 : 0);",
+     "float fa = *(const float*)a, fb = *(const float*)b;\n    (void)x; (void)y;\n    return fa < fb ? -1 : (fa > fb ? 1 : 0);"),
+    ("median_sum_in_single", "out = (float)(((double)v[size / 2 - 1] + (double)v[size / 2]) / 2.0);",
+     "out = (v[size / 2 - 1] + v[size / 2]) / 2.0f;"),
     ("buffer_keeps_k_plus", "if (*size == k && !entry_less(dist, id, buf[k - 1].dist, buf[k - 1].id)) return 0;",
      "if (*size == k && !entry_less(dist, id, buf[k - 1].dist, buf[k - 1].id)) return 1;"),
 ]

@@ -316,3 +316,62 @@ def test_mean_sums_in_double():
     g = oracle.Grid(x, y, 100.0)
     _, _, pred = g.query(np.array([[0.0]], np.float32), 3, 1)
     assert pred[0] == np.float32(1.0 / 3.0)
+
+
+# ---- median head (Sec. I and Sec. III.D name the median beside the average) ----
+
+def _one_dim_grid(y):
+    x = np.arange(1, len(y) + 1, dtype=np.float32).reshape(-1, 1)  # distances 1, 2, ... from 0
+    return oracle.Grid(x, np.asarray(y, np.float32), 1000.0)
+
+
+def test_median_of_known_values():
+    g = _one_dim_grid([5.0, -1.0, 3.0, 2.0, 1000.0])
+    q = np.array([[0.0]], np.float32)
+    for k, expect in [(1, 5.0), (2, 2.0), (3, 3.0), (4, 2.5), (5, 3.0)]:
+        _, _, pred = g.query(q, k, 2)
+        assert pred[0] == np.float32(expect), k
+
+
+def test_median_matches_statistics_median():
+    """Against Python's statistics.median of the outputs of the neighbours the walk found."""
+    import statistics
+
+    for seed, (n, d, k, w) in enumerate([(300, 2, 5, 0.1), (300, 3, 8, 0.2), (40, 1, 7, 0.05),
+                                         (200, 4, 32, 0.3), (5, 2, 9, 0.5)]):
+        x, _, q = wl.uniform(n, 20, d, seed=100 + seed)
+        rng = np.random.default_rng(seed)
+        y = rng.integers(-4, 5, size=n).astype(np.float32) * np.float32(0.75)  # many equal outputs
+        g = oracle.Grid(x, y, w)
+        ids, _, pred = g.query(q, k, 2)
+        for i in range(q.shape[0]):
+            vals = [float(y[j]) for j in ids[i] if j >= 0]
+            assert pred[i] == np.float32(statistics.median(vals)), (seed, i)
+
+
+def test_median_signed_zero_by_total_order():
+    """-0 sorts before +0: the middle of {+0, -0, -0} is -0, of {-0, +0, +0} is +0."""
+    q = np.array([[0.0]], np.float32)
+    _, _, pred = _one_dim_grid([0.0, -0.0, -0.0]).query(q, 3, 2)
+    assert pred.view(np.uint32)[0] == 0x80000000
+    _, _, pred = _one_dim_grid([-0.0, 0.0, 0.0]).query(q, 3, 2)
+    assert pred.view(np.uint32)[0] == 0
+    # zeros met in the order +0, -0: sorted -0, +0 whatever the neighbour order
+    _, _, pred = _one_dim_grid([0.0, -0.0, 1.0]).query(q, 3, 2)
+    assert pred.view(np.uint32)[0] == 0
+    _, _, pred = _one_dim_grid([0.0, -0.0, -1.0]).query(q, 3, 2)
+    assert pred.view(np.uint32)[0] == 0x80000000
+
+
+def test_median_even_count_sums_in_double():
+    """(a + b) / 2 in double: finite even where a float sum of a and b overflows."""
+    a, b = np.float32(3.0e38), np.float32(3.2e38)
+    _, _, pred = _one_dim_grid([a, b, 1.0, 1.0]).query(np.array([[0.0]], np.float32), 2, 2)
+    assert np.isfinite(pred[0])
+    assert pred[0] == np.float32((float(a) + float(b)) / 2.0)
+
+
+def test_median_with_fewer_points_than_k_and_none():
+    q = np.array([[0.0]], np.float32)
+    _, _, pred = _one_dim_grid([4.0, 1.0, 9.0]).query(q, 6, 2)
+    assert pred[0] == np.float32(4.0)
