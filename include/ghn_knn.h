@@ -53,10 +53,15 @@ extern "C" {
 #define KNN_ELIMIT 4 /* a query reached the layer cap; its rows are -1 / +inf */
 typedef int32_t knn_status;
 
-/* Prediction modes (Sec. I: majority class, or average of the outputs). */
-#define KNN_NONE -1 /* neighbours only; pred is ignored and may be NULL */
-#define KNN_VOTE 0  /* labels are int32 classes; pred receives int32 */
-#define KNN_MEAN 1  /* labels are float targets; pred receives float */
+/* Prediction modes (Sec. I and Sec. III.D: majority class, or the average
+ * or the median of the outputs). */
+#define KNN_NONE -1  /* neighbours only; pred is ignored and may be NULL */
+#define KNN_VOTE 0   /* labels are int32 classes; pred receives int32 */
+#define KNN_MEAN 1   /* labels are float targets; pred receives float */
+#define KNN_MEDIAN 2 /* labels are float targets; pred receives float: the
+                        middle output under IEEE total order (-0 < +0), or
+                        the two middle ones a, b averaged as
+                        (double(a) + double(b)) / 2 for an even count */
 
 /* Cell tables (Sec. III.A: a hash table keyed by the cell id, no empty cells). */
 #define KNN_TABLE_AUTO 0  /* dense when the cell box has at most 4n + 1024 cells */
@@ -108,10 +113,12 @@ knn_status knn_build(const float* points, const void* labels, int64_t n, int32_t
  *   queries  host or device, m*d float32, row-major.
  *   m        m >= 0 (0 is a no-op).
  *   k        1 <= k <= 64.
- *   mode     KNN_NONE / KNN_VOTE / KNN_MEAN (VOTE and MEAN need labels).
+ *   mode     KNN_NONE / KNN_VOTE / KNN_MEAN / KNN_MEDIAN (all but NONE need
+ *            labels).
  *   ids      host or device, m*k int32: training indices, nearest first.
  *   dist2    host or device, m*k float32 squared distances (may be NULL).
- *   pred     host or device, m int32 (VOTE) or float32 (MEAN), or NULL.
+ *   pred     host or device, m int32 (VOTE) or float32 (MEAN, MEDIAN), or
+ *            NULL; NaN for MEAN / MEDIAN when no neighbour was found.
  *   flags    KNN_QUERY_CHECKED | KNN_QUERY_SORTED.
  *   stream   cudaStream_t or NULL.
  * Device outputs are written asynchronously on `stream`; host outputs are

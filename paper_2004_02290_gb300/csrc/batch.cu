@@ -751,7 +751,7 @@ knn_status plan_layout(const ghn_batch* b, const float* const* queries, const in
     for (int i = 0; i < b->count; ++i) {
         char msg[160];
         if (m[i] < 0 || m[i] >= (1ll << 31) || k[i] < 1 || k[i] > kMaxK || mode[i] < -1 ||
-            mode[i] > 1) {
+            mode[i] > 2) {
             snprintf(msg, sizeof(msg), "knn_batch_query: index %d: bad m, k or mode", i);
             set_error(msg);
             return KNN_EINVAL;

@@ -616,7 +616,7 @@ knn_status check_query_args(const ghn_index* x, const float* queries, long long 
         set_err("knn_query: k = %d outside [1, %d]", k, kMaxK);
         return KNN_EINVAL;
     }
-    if (mode < -1 || mode > 1) {
+    if (mode < -1 || mode > 2) {
         set_err("knn_query: unknown mode %d", mode);
         return KNN_EINVAL;
     }

@@ -83,8 +83,8 @@ extern "C" knn_status knn_query_noalloc(const ghn_index* index, const float* que
                        "holds at most 1048576 queries per call");
         return KNN_EINVAL;
     }
-    if (k < 1 || k > ghn::kMaxK || mode < -1 || mode > 1) {
-        ghn::set_error("knn_query_noalloc: k must be in [1, 64] and mode in {-1, 0, 1}");
+    if (k < 1 || k > ghn::kMaxK || mode < -1 || mode > 2) {
+        ghn::set_error("knn_query_noalloc: k must be in [1, 64] and mode in {-1, 0, 1, 2}");
         return KNN_EINVAL;
     }
     if (mode >= 0 && !ghn::index_has_labels(index)) {

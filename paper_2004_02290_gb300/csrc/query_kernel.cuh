@@ -480,6 +480,25 @@ __device__ __forceinline__ void row_ranges(const QueryArgs& a, unsigned long lon
         }
     }
     sa = la = sb = lb = 0u;
+    if (prune && kth_d <= 3.0e38f) {
+        // along the row's own axis only the cells within the radius left over
+        // by the outer axes, sqrt(kth_d - og2), can hold a point that enters:
+        // clip both runs to them (approximate root, widened as in layer_box).
+        // An infinite k-th distance (overflowed squares) clips nothing.
+        const float rem = kth_d * (1.0f + 2e-5f) - og2;
+        if (rem < 0.0f) return;
+        const float r = (rem > 0.0f ? rem * rsqrtf(rem) : 0.0f) * a.g.inv_w * (1.0f + 1e-4f);
+        const float u = s.u[dl];
+        const float m = 1e-5f * (fabsf(u) + r) + 1e-3f;
+        const float c0f = floorf(u - r - m), c1f = floorf(u + r + m);
+        // the clip only matters inside the row's 32-bit coordinate range
+        const long long c0 = c0f <= -2147483520.0f ? (long long)INT_MIN : (long long)c0f;
+        const long long c1 = c1f >= 2147483520.0f ? (long long)INT_MAX : (long long)c1f;
+        x0a = x0a > c0 ? x0a : c0;
+        x1a = x1a < c1 ? x1a : c1;
+        x0b = x0b > c0 ? x0b : c0;
+        x1b = x1b < c1 ? x1b : c1;
+    }
     if (x0a <= x1a &&
         !(prune && (og2 + axis_gap2(x0a, x1a, s.u[dl], a.g.w)) * (1.0f - 1e-5f) > kth_d))
         resolve_run<DENSE>(a, hmask, base, x0a, x1a, counting, sa, la, cells);
@@ -615,6 +634,56 @@ __device__ __forceinline__ void write_outputs(const QueryArgs& a, long long qid,
             static_cast<float*>(a.pred)[qid] =
                 found ? __double2float_rn(__ddiv_rn(sum, (double)found))
                       : __int_as_float(0x7fc00000);
+    } else if (a.mode == 2 && a.pred) {
+        // median of the found neighbours' outputs (Sec. I, Sec. III.D): each
+        // value's rank under IEEE total order (ties by neighbour position),
+        // then the one or two middle values; an even count averages them in
+        // double
+        unsigned int key[NS];
+        float y[NS];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            const bool v = i * 32 + lane < found;
+            const unsigned int u = v ? __ldg(a.labels + (unsigned int)tk.s[i]) : 0u;
+            y[i] = __uint_as_float(u);
+            key[i] = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+        }
+        int rank[NS];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) rank[i] = 0;
+        for (int e = 0; e < found; ++e) {
+            unsigned int other;
+            if constexpr (NS == 1) {
+                other = __shfl_sync(FULL, key[0], e);
+            } else {
+                const unsigned int o0 = __shfl_sync(FULL, key[0], e & 31);
+                const unsigned int o1 = __shfl_sync(FULL, key[1], e & 31);
+                other = e < 32 ? o0 : o1;
+            }
+#pragma unroll
+            for (int i = 0; i < NS; ++i)
+                rank[i] += other < key[i] || (other == key[i] && e < i * 32 + lane);
+        }
+        const int lo = (found - 1) >> 1, hi = found >> 1;
+        float vlo = 0.0f, vhi = 0.0f;
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            const bool v = i * 32 + lane < found;
+            const unsigned int blo = __ballot_sync(FULL, v && rank[i] == lo);
+            const unsigned int bhi = __ballot_sync(FULL, v && rank[i] == hi);
+            const float fl = __shfl_sync(FULL, y[i], blo ? __ffs(blo) - 1 : 0);
+            const float fh = __shfl_sync(FULL, y[i], bhi ? __ffs(bhi) - 1 : 0);
+            if (blo) vlo = fl;
+            if (bhi) vhi = fh;
+        }
+        if (lane == 0) {
+            float out = __int_as_float(0x7fc00000);
+            if (found & 1)
+                out = vlo;
+            else if (found)
+                out = __double2float_rn(__dmul_rn(__dadd_rn((double)vlo, (double)vhi), 0.5));
+            static_cast<float*>(a.pred)[qid] = out;
+        }
     }
 }
 

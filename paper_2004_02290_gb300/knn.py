@@ -14,7 +14,7 @@ import threading
 import numpy as np
 
 KNN_OK, KNN_EINVAL, KNN_ENOMEM, KNN_ECUDA, KNN_ELIMIT = 0, 1, 2, 3, 4
-KNN_NONE, KNN_VOTE, KNN_MEAN = -1, 0, 1
+KNN_NONE, KNN_VOTE, KNN_MEAN, KNN_MEDIAN = -1, 0, 1, 2
 KNN_TABLE_AUTO, KNN_TABLE_DENSE, KNN_TABLE_HASH = 0, 1, 2
 KNN_QUERY_CHECKED, KNN_QUERY_SORTED = 1, 2
 

@@ -33,7 +33,7 @@ def _dev(a):
 
 
 def _problems():
-    """Uneven problems over every dimension, k up to 64, both modes and tables."""
+    """Uneven problems over every dimension, k up to 64, every head and both tables."""
     ps = wl.gen_batched(20, seed=11, n_lo=300, n_hi=30_000, dims=(1, 2, 3, 4, 5, 6, 7, 8),
                         ks=(1, 5, 15, 32, 40, 64))
     tables = []
@@ -41,6 +41,8 @@ def _problems():
     for i, p in enumerate(ps):
         p.w = float(np.float32(0.05 * (1.0 + (i % 4)) * (p.d / 3.0)))
         tables.append(int(rng.choice([knn.KNN_TABLE_AUTO, knn.KNN_TABLE_HASH])))
+        if i % 4 == 3:
+            p.mode = knn.KNN_MEDIAN  # a regression problem with the median head
     # a problem with far queries and one with a single occupied cell
     ps[3].queries[:3] = np.float32(40.0)
     ps[5].w = 1000.0

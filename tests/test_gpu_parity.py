@@ -65,6 +65,8 @@ def assert_same(got, exp, mode):
         rel = np.abs(pred.astype(np.float64) - e_pred) / np.maximum(np.abs(e_pred), 1e-30)
         assert rel.max() <= MEAN_RTOL
         assert np.array_equal(pred.view(np.uint32), e_pred.view(np.uint32))
+    elif mode == knn.KNN_MEDIAN:
+        assert np.array_equal(pred.view(np.uint32), e_pred.view(np.uint32))
 
 
 # ---- the tiny workload, every output ----
@@ -131,6 +133,30 @@ def test_uniform_cases(d, n, m, w, k, mode, table):
     q = np.concatenate([q, extra]).astype(np.float32)
     got, info = gpu_run(x, lab, q, w, k, mode, table)
     assert_same(got, oracle_run(x, lab, q, w, k, mode), mode)
+
+
+@pytest.mark.parametrize("table", [knn.KNN_TABLE_DENSE, knn.KNN_TABLE_HASH])
+@pytest.mark.parametrize("d,n,m,w,k", [(2, 5000, 400, 0.02, 1), (2, 5000, 400, 0.02, 10),
+                                       (3, 6000, 300, 0.06, 15), (4, 6000, 300, 0.12, 32),
+                                       (4, 6000, 300, 0.12, 64), (6, 3000, 150, 0.35, 33)])
+def test_median_cases(d, n, m, w, k, table):
+    """Median head: bit-exact, with many equal outputs, signed zeros and even counts."""
+    x, _, q = wl.uniform(n, m, d, seed=2000 + 13 * d + k)
+    rng = np.random.default_rng(d + k)
+    lab = (rng.integers(-3, 4, size=n) * 0.5).astype(np.float32)
+    lab[rng.random(n) < 0.1] = np.float32(-0.0)
+    q = np.concatenate([q, np.full((1, d), -0.3, np.float32)]).astype(np.float32)
+    got, _ = gpu_run(x, lab, q, w, k, knn.KNN_MEDIAN, table)
+    assert_same(got, oracle_run(x, lab, q, w, k, knn.KNN_MEDIAN), knn.KNN_MEDIAN)
+
+
+def test_median_fewer_points_than_k():
+    x = np.array([[0.1, 0.1], [0.2, 0.3], [0.9, 0.9]], np.float32)
+    lab = np.array([3.0, -1.0, 2.0], np.float32)
+    q = np.array([[0.0, 0.0], [1.0, 1.0]], np.float32)
+    got, _ = gpu_run(x, lab, q, 0.25, 8, knn.KNN_MEDIAN)
+    assert_same(got, oracle_run(x, lab, q, 0.25, 8, knn.KNN_MEDIAN), knn.KNN_MEDIAN)
+    assert got[2][0] == np.float32(2.0)
 
 
 def test_lattice_ties():
@@ -398,17 +424,19 @@ cases.append((cw.points, cw.labels, cw.queries, cw.w, 16))
 bad = 0
 for x, lab, q, w, k in cases:
     g = oracle.Grid(x, lab, w)
-    e_ids, e_d2, e_pred = g.query(q, k, 0 if lab.dtype == np.int32 else 1)
-    for table in (knn.KNN_TABLE_DENSE, knn.KNN_TABLE_HASH):
-        idx = knn.knn_build(dev(x), dev(lab), w, table)
-        mode = knn.KNN_VOTE if lab.dtype == np.int32 else knn.KNN_MEAN
-        ids, d2, pred = idx.query(dev(q), k, mode, flags=knn.KNN_QUERY_CHECKED | knn.KNN_QUERY_SORTED)
-        torch.cuda.synchronize()
-        ok = (np.array_equal(ids.cpu().numpy(), e_ids)
-              and np.array_equal(d2.cpu().numpy().view(np.uint32), e_d2.view(np.uint32))
-              and np.array_equal(pred.cpu().numpy().view(np.uint32), e_pred.view(np.uint32)))
-        bad += not ok
-        idx.free()
+    modes = [knn.KNN_VOTE] if lab.dtype == np.int32 else [knn.KNN_MEAN, knn.KNN_MEDIAN]
+    for mode in modes:
+        e_ids, e_d2, e_pred = g.query(q, k, mode)
+        for table in (knn.KNN_TABLE_DENSE, knn.KNN_TABLE_HASH):
+            idx = knn.knn_build(dev(x), dev(lab), w, table)
+            ids, d2, pred = idx.query(dev(q), k, mode,
+                                      flags=knn.KNN_QUERY_CHECKED | knn.KNN_QUERY_SORTED)
+            torch.cuda.synchronize()
+            ok = (np.array_equal(ids.cpu().numpy(), e_ids)
+                  and np.array_equal(d2.cpu().numpy().view(np.uint32), e_d2.view(np.uint32))
+                  and np.array_equal(pred.cpu().numpy().view(np.uint32), e_pred.view(np.uint32)))
+            bad += not ok
+            idx.free()
 print("BAD", bad)
 """
 
