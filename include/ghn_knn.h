@@ -51,6 +51,7 @@ extern "C" {
 #define KNN_ENOMEM 2 /* device or host allocation failed */
 #define KNN_ECUDA 3  /* a CUDA call failed; knn_last_error() has its text */
 #define KNN_ELIMIT 4 /* a query reached the layer cap; its rows are -1 / +inf */
+#define KNN_ETIMEDOUT 5 /* a wait ended before the request completed (ghn_serve.h) */
 typedef int32_t knn_status;
 
 /* Prediction modes (Sec. I and Sec. III.D: majority class, or the average

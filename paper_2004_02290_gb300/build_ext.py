@@ -18,7 +18,7 @@ LIB = os.path.join(OUT_DIR, "libghn_knn.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["capi.cu", "build_kernels.cu", "query_d12.cu", "query_d34.cu", "query_d56.cu",
-           "query_d78.cu", "noalloc.cu", "batch.cu"]
+           "query_d78.cu", "noalloc.cu", "batch.cu", "serve.cu"]
 HEADERS = ["ghn_internal.cuh", "query_kernel.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -44,7 +44,8 @@ def _stale(target: str, deps) -> bool:
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
     nvcc = _nvcc()
-    hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(INCLUDE, "ghn_knn.h")]
+    hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(INCLUDE, h)
+                                                        for h in ("ghn_knn.h", "ghn_serve.h")]
 
     def compile_one(src):
         path = os.path.join(CSRC, src)

@@ -670,6 +670,16 @@ void index_query_args(const ghn_index* x, QueryArgs& a)
 
 void index_mark_use(const ghn_index* x, cudaStream_t s) { cudaEventRecord(x->last_use, s); }
 
+long long index_bytes(const ghn_index* x)
+{
+    long long b = x->n * (long long)row_floats(x->d) * 4 + x->n * 4;  // rows, rid
+    if (x->labels) b += x->n * 4;
+    if (x->dstart) b += ((long long)x->ncell_space + 1) * 4;
+    if (x->slots) b += (long long)x->max_slots * (long long)sizeof(HashSlot);
+    if (x->bitmap) b += (long long)((x->ncell_space + 31ull) / 32ull) * 4;
+    return b + (long long)sizeof(GridDev);
+}
+
 cudaError_t launch_batch_query(const BatchArgs& g, int sms, cudaStream_t s)
 {
     count_launches(1);

@@ -178,6 +178,7 @@ bool index_has_labels(const ghn_index* x);
 int index_dims(const ghn_index* x);
 void index_query_args(const ghn_index* x, QueryArgs& a);  // the index's part of QueryArgs
 void index_mark_use(const ghn_index* x, cudaStream_t s);
+long long index_bytes(const ghn_index* x);  // device bytes the index holds
 
 // Allocation through the library's pool (with the GHN_FAIL_ALLOC_AT injector).
 int device_alloc(void** p, size_t bytes, cudaStream_t s, const char* what);

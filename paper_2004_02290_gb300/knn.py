@@ -1,4 +1,4 @@
-"""Thin ctypes binding of the C ABI in ``include/ghn_knn.h``.
+"""Thin ctypes binding of the C ABI in ``include/ghn_knn.h`` and ``include/ghn_serve.h``.
 
 Argument marshalling only: every step of index build and query runs in the
 CUDA library ``_build/libghn_knn.so``.  There is no fallback: if the library
@@ -13,7 +13,7 @@ import threading
 
 import numpy as np
 
-KNN_OK, KNN_EINVAL, KNN_ENOMEM, KNN_ECUDA, KNN_ELIMIT = 0, 1, 2, 3, 4
+KNN_OK, KNN_EINVAL, KNN_ENOMEM, KNN_ECUDA, KNN_ELIMIT, KNN_ETIMEDOUT = 0, 1, 2, 3, 4, 5
 KNN_NONE, KNN_VOTE, KNN_MEAN, KNN_MEDIAN = -1, 0, 1, 2
 KNN_TABLE_AUTO, KNN_TABLE_DENSE, KNN_TABLE_HASH = 0, 1, 2
 KNN_QUERY_CHECKED, KNN_QUERY_SORTED = 1, 2
@@ -44,7 +44,32 @@ EXPORTED = ["knn_batch_build", "knn_batch_info", "knn_batch_query", "knn_batch_p
             "knn_build", "knn_query", "knn_query_stats", "knn_query_noalloc", "knn_index_info",
             "knn_index_export",
             "knn_timing_enable", "knn_timing_read", "knn_kernel_launches", "knn_free",
-            "knn_last_error", "knn_abi_version"]
+            "knn_last_error", "knn_abi_version",
+            "knn_server_create", "knn_server_build", "knn_server_drop", "knn_server_submit",
+            "knn_server_wait", "knn_server_test", "knn_server_stats", "knn_server_clock_ns",
+            "knn_server_build_bytes", "knn_server_destroy"]
+
+
+class knn_server_config(ctypes.Structure):
+    _fields_ = [("memory_budget", ctypes.c_int64), ("max_batch_queries", ctypes.c_int64),
+                ("max_batch_outputs", ctypes.c_int64), ("max_batch_requests", ctypes.c_int32),
+                ("max_inflight", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class knn_ticket_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("kind", ctypes.c_int32),
+                ("index_id", ctypes.c_int64), ("batch", ctypes.c_int64),
+                ("t_submit_ns", ctypes.c_int64), ("t_dispatch_ns", ctypes.c_int64),
+                ("t_done_ns", ctypes.c_int64)]
+
+
+class knn_server_stats_t(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in (
+        "batches", "requests_done", "queries_done", "builds_done", "drops_done", "indexes",
+        "resident_bytes", "reserved_bytes", "buffer_bytes", "budget_bytes", "queued_requests",
+        "waiting_builds", "inflight_batches", "max_batch_requests_seen",
+        "max_batch_queries_seen")]
 
 
 def library(path: str | None = None) -> ctypes.CDLL:
@@ -103,6 +128,28 @@ def library(path: str | None = None) -> ctypes.CDLL:
         lib.knn_plan_free.restype = None
         lib.knn_batch_free.argtypes = [vp]
         lib.knn_batch_free.restype = None
+        pi64 = ctypes.POINTER(i64)
+        lib.knn_server_create.argtypes = [ctypes.POINTER(knn_server_config), ctypes.POINTER(vp)]
+        lib.knn_server_create.restype = i32
+        lib.knn_server_build.argtypes = [vp, vp, vp, i64, i32, ctypes.c_float, i32, pi64, pi64]
+        lib.knn_server_build.restype = i32
+        lib.knn_server_drop.argtypes = [vp, i64, pi64]
+        lib.knn_server_drop.restype = i32
+        lib.knn_server_submit.argtypes = [vp, i64, vp, i64, i32, i32, vp, vp, vp, pi64]
+        lib.knn_server_submit.restype = i32
+        lib.knn_server_wait.argtypes = [vp, i64, i64, ctypes.POINTER(knn_ticket_info)]
+        lib.knn_server_wait.restype = i32
+        lib.knn_server_test.argtypes = [vp, i64, ctypes.POINTER(i32),
+                                        ctypes.POINTER(knn_ticket_info)]
+        lib.knn_server_test.restype = i32
+        lib.knn_server_stats.argtypes = [vp, ctypes.POINTER(knn_server_stats_t)]
+        lib.knn_server_stats.restype = i32
+        lib.knn_server_clock_ns.argtypes = []
+        lib.knn_server_clock_ns.restype = i64
+        lib.knn_server_build_bytes.argtypes = [i64, i32, i32]
+        lib.knn_server_build_bytes.restype = i64
+        lib.knn_server_destroy.argtypes = [vp]
+        lib.knn_server_destroy.restype = None
         _lib = lib
         return lib
 
@@ -417,3 +464,110 @@ def knn_kernel_launches() -> int:
 
 def knn_last_error() -> str:
     return library().knn_last_error().decode(errors="replace")
+
+
+# ---- serving engine (include/ghn_serve.h) ----
+
+class Server:
+    """A serving engine: resident indexes, memory-admitted builds, continuous batching.
+
+    Requests return tickets at once; ``wait`` returns a ticket's outcome.  The
+    host arrays of a request (numpy) are kept alive here until its ticket is
+    waited for.
+    """
+
+    def __init__(self, memory_budget: int = 0, max_batch_queries: int = 0,
+                 max_batch_outputs: int = 0, max_batch_requests: int = 0, max_inflight: int = 0,
+                 device: int = 0):
+        cfg = knn_server_config(memory_budget, max_batch_queries, max_batch_outputs,
+                                max_batch_requests, max_inflight, device, 0)
+        h = ctypes.c_void_p()
+        _check(library().knn_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self._keep = {}  # ticket -> arrays the request borrows or fills
+        self._klock = threading.Lock()
+
+    def build(self, points, labels=None, cell_width: float = 1.0, table: int = KNN_TABLE_AUTO):
+        """Request a new index; returns (index_id, ticket)."""
+        n, d = int(points.shape[0]), int(points.shape[1])
+        pp, kp = _ptr(points)
+        lp, kl = _ptr(labels)
+        iid, t = ctypes.c_int64(), ctypes.c_int64()
+        _check(library().knn_server_build(self._h, pp, lp, n, d,
+                                          ctypes.c_float(float(np.float32(cell_width))), table,
+                                          ctypes.byref(iid), ctypes.byref(t)))
+        with self._klock:
+            self._keep[t.value] = (points, labels, kp, kl)
+        return iid.value, t.value
+
+    def drop(self, index_id: int) -> int:
+        t = ctypes.c_int64()
+        _check(library().knn_server_drop(self._h, index_id, ctypes.byref(t)))
+        return t.value
+
+    def submit(self, index_id: int, queries: np.ndarray, k: int, mode: int = KNN_NONE,
+               want_dist2: bool = True):
+        """Queue a query request (host arrays); returns (ticket, ids, dist2, pred)."""
+        q = np.ascontiguousarray(queries, np.float32)
+        m = int(q.shape[0])
+        ids = np.empty((m, k), np.int32)
+        d2 = np.empty((m, k), np.float32) if want_dist2 else None
+        pred = None
+        if mode >= 0:
+            pred = np.empty(m, np.int32 if mode == KNN_VOTE else np.float32)
+        t = ctypes.c_int64()
+        _check(library().knn_server_submit(
+            self._h, index_id, q.ctypes.data, m, k, mode, ids.ctypes.data,
+            d2.ctypes.data if d2 is not None else None,
+            pred.ctypes.data if pred is not None else None, ctypes.byref(t)))
+        with self._klock:
+            self._keep[t.value] = (q, ids, d2, pred)
+        return t.value, ids, d2, pred
+
+    def wait(self, ticket: int, timeout_us: int = -1):
+        """Outcome of a ticket (knn_ticket_info), or None if the timeout ran out."""
+        info = knn_ticket_info()
+        rc = library().knn_server_wait(self._h, ticket, timeout_us, ctypes.byref(info))
+        if rc == KNN_ETIMEDOUT:
+            return None
+        _check(rc)
+        with self._klock:
+            self._keep.pop(ticket, None)
+        return info
+
+    def test(self, ticket: int):
+        info = knn_ticket_info()
+        done = ctypes.c_int32()
+        _check(library().knn_server_test(self._h, ticket, ctypes.byref(done), ctypes.byref(info)))
+        if not done.value:
+            return None
+        with self._klock:
+            self._keep.pop(ticket, None)
+        return info
+
+    def stats(self) -> knn_server_stats_t:
+        s = knn_server_stats_t()
+        _check(library().knn_server_stats(self._h, ctypes.byref(s)))
+        return s
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            library().knn_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def knn_server_build_bytes(n: int, d: int, labels: bool) -> int:
+    """Bytes a build of n points in d dimensions is admitted with (its footprint bound)."""
+    return int(library().knn_server_build_bytes(n, d, int(bool(labels))))
+
+
+def knn_server_clock_ns() -> int:
+    """The serving engine's clock (CLOCK_MONOTONIC, ns); equals time.monotonic_ns()."""
+    return int(library().knn_server_clock_ns())

@@ -9,7 +9,7 @@ import pytest
 from paper_2004_02290_gb300 import knn
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "ghn_knn.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("ghn_knn.h", "ghn_serve.h")]
 
 
 @pytest.fixture(scope="module")
@@ -21,8 +21,10 @@ def lib():
 
 
 def _declared():
-    with open(HEADER) as f:
-        text = f.read()
+    text = ""
+    for h in HEADERS:
+        with open(h) as f:
+            text += f.read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(knn_[a-z_]+)\s*\(", text)))
 
@@ -126,3 +128,39 @@ def test_batch_build_rejects_bad_arguments(lib):
     assert not h.value
     lib.knn_batch_free(None)
     lib.knn_plan_free(None)
+
+
+def test_server_rejects_bad_arguments_on_the_host(lib):
+    """Checks that need no GPU: NULL pointers, bad configuration fields, bad requests."""
+    h = ctypes.c_void_p()
+    assert lib.knn_server_create(None, None) == knn.KNN_EINVAL
+    bad = knn.knn_server_config(0, 0, 0, 0, 0, 0, 7)  # reserved must be 0
+    assert lib.knn_server_create(ctypes.byref(bad), ctypes.byref(h)) == knn.KNN_EINVAL
+    assert not h.value
+    bad = knn.knn_server_config(0, -5, 0, 0, 0, 0, 0)
+    assert lib.knn_server_create(ctypes.byref(bad), ctypes.byref(h)) == knn.KNN_EINVAL
+    t = ctypes.c_int64()
+    assert lib.knn_server_submit(None, 1, None, 0, 5, -1, None, None, None,
+                                 ctypes.byref(t)) == knn.KNN_EINVAL
+    assert lib.knn_server_wait(None, 1, 0, None) == knn.KNN_EINVAL
+    assert lib.knn_server_drop(None, 1, ctypes.byref(t)) == knn.KNN_EINVAL
+    assert lib.knn_server_stats(None, None) == knn.KNN_EINVAL
+    lib.knn_server_destroy(None)
+
+
+def test_server_build_bound_grows_with_n(lib):
+    a = lib.knn_server_build_bytes(1000, 3, 1)
+    b = lib.knn_server_build_bytes(2000, 3, 1)
+    assert 0 < a < b
+    assert lib.knn_server_build_bytes(1000, 6, 1) > a  # wider rows
+    assert lib.knn_server_build_bytes(0, 3, 1) == 0
+    assert lib.knn_server_build_bytes(10, 9, 1) == 0
+
+
+def test_server_clock_is_monotonic_ns(lib):
+    import time
+
+    a = time.monotonic_ns()
+    c = lib.knn_server_clock_ns()
+    b = time.monotonic_ns()
+    assert a <= c <= b
