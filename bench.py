@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import argparse
 import concurrent.futures as cf
+import ctypes
 import hashlib
 import json
 import os
@@ -49,7 +50,13 @@ def parse_args(argv=None):
     p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--config", default="large_cls", choices=list(wl.SPECS) + ["batched"])
+    p.add_argument("--config", default="large_cls",
+                   choices=list(wl.SPECS) + ["batched", "serving"])
+    p.add_argument("--serve-seconds", type=float, default=10.0,
+                   help="serving: length of the Poisson arrival window")
+    p.add_argument("--serve-rate", type=float, default=2000.0,
+                   help="serving: query requests per second")
+    p.add_argument("--serve-indexes", type=int, default=64, help="serving: resident indexes")
     p.add_argument("--batch-count", type=int, default=256,
                    help="problems of the batched workload")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -535,12 +542,239 @@ def run_batched(args):
     }), flush=True)
 
 
+def _pace(sched_ns: int):
+    """Wait until the monotonic clock reaches sched_ns (sleep, then spin the last 150 us)."""
+    while True:
+        now = time.monotonic_ns()
+        if now >= sched_ns:
+            return now
+        if sched_ns - now > 300_000:
+            time.sleep((sched_ns - now - 150_000) * 1e-9)
+
+
+def _pct(v, q):
+    return float(np.percentile(np.asarray(v, np.float64), q)) if len(v) else None
+
+
+def run_serving(args):
+    """Continuous-batching server against the plain form on the serving workload.
+
+    64 resident indexes (n log-uniform in [1e4, 5e7], d in 2..6, at most 60 GB)
+    are built through the server, each with the autotuner's width.  Query
+    requests (1..4096 queries, k in {5, 16}) arrive as a Poisson process at
+    --serve-rate per second, with index builds interleaved (each admitted by
+    memory; an older extra index is dropped after each).  Reported:
+      - under that load, per-request latency from the scheduled arrival to the
+        results in the caller's host buffers (p50 / p99), for the server and
+        for the plain form (one knn_query per request, in arrival order);
+      - capacity: every request at once, queries per second of the server and
+        of the plain form, and whether their outputs are identical.
+    """
+    import threading
+
+    import torch
+
+    import __graft_entry__
+    from paper_2004_02290_gb300 import autotune, knn
+
+    __graft_entry__.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    sys.setswitchinterval(2e-4)
+    lib = knn.library()
+    specs = wl.gen_serving_indexes(count=args.serve_indexes)
+    events = wl.gen_serving_requests(specs, rate=args.serve_rate, duration=args.serve_seconds)
+    qev = [e for e in events if e.kind == "query"]
+    bev = [e for e in events if e.kind == "build"]
+    srv = knn.Server(memory_budget=60 << 30)
+
+    # ---- resident indexes: autotuned width (k = 16), built through the server ----
+    t_setup = time.perf_counter()
+    ids, tune_s = [], 0.0
+    for ix in specs:
+        pts, lab = wl.serving_points(ix, dev)
+        qs = torch.from_numpy(wl.serving_queries(ix, 4096, np.random.default_rng(ix.seed))).to(dev)
+        t0 = time.perf_counter()
+        w = autotune.tune_width(pts, lab, qs, 16, ix.mode, dev=dev).width
+        tune_s += time.perf_counter() - t0
+        iid, t = srv.build(pts, lab, w)
+        info = srv.wait(t)
+        if info.status != knn.KNN_OK:
+            raise RuntimeError(f"build of a resident index failed: status {info.status}")
+        ids.append(iid)
+        del pts, lab, qs
+    # points of the interleaved builds, drawn before the clock starts
+    extra = []
+    for e in bev:
+        pts, lab = wl.serving_points(e.spec, dev)
+        extra.append((pts, lab, autotune.start_width(pts, 16)))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_setup
+    st0 = srv.stats()
+    plain_idx = [srv.index(i) for i in ids]
+
+    # ---- warm-up: a burst of the first requests through both forms ----
+    for e in qev[: min(200, len(qev))]:
+        t, *_ = srv.submit(ids[e.index], e.queries, e.k, e.mode)
+        srv.wait(t)
+        plain_idx[e.index].query(e.queries, e.k, e.mode, flags=knn.KNN_QUERY_CHECKED)
+
+    sampler = ClockSampler(0)
+    sampler.start()
+    l0 = knn.knn_kernel_launches()
+
+    # ---- server under Poisson arrivals ----
+    import queue as _queue
+
+    pending = _queue.Queue()
+    lat, lag, batches, bstats, done_ns = [], [], set(), [], [0]
+    kept_extra = []
+
+    def waiter():
+        while True:
+            item = pending.get()
+            if item is None:
+                return
+            kind, ticket, sched = item
+            info = srv.wait(ticket)
+            if kind == "query":
+                done_ns[0] = max(done_ns[0], info.t_done_ns)
+                lat.append((info.t_done_ns - sched) * 1e-6)
+                lag.append((info.t_submit_ns - sched) * 1e-6)
+                batches.add(info.batch)
+            else:
+                bstats.append(((info.t_done_ns - sched) * 1e-6,
+                               (info.t_dispatch_ns - info.t_submit_ns) * 1e-6, info.status))
+                kept_extra.append(info.index_id)
+                if len(kept_extra) > 2:  # keep the two newest extra indexes
+                    srv.wait(srv.drop(kept_extra.pop(0)))
+
+    th = threading.Thread(target=waiter)
+    th.start()
+    base = time.monotonic_ns() + 20_000_000
+    bi = 0
+    for e in events:
+        sched = base + int(e.t * 1e9)
+        _pace(sched)
+        if e.kind == "query":
+            t, *_ = srv.submit(ids[e.index], e.queries, e.k, e.mode, want_dist2=False)
+            pending.put(("query", t, sched))
+        else:
+            pts, lab, w = extra[bi]
+            bi += 1
+            _, t = srv.build(pts, lab, w)
+            pending.put(("build", t, sched))
+    pending.put(None)
+    th.join()
+    poisson_s = (done_ns[0] - base) * 1e-9
+    st1 = srv.stats()
+    q_total = sum(e.queries.shape[0] for e in qev)
+
+    # ---- capacity: every request at once; lean calls with preallocated buffers ----
+    outs_s, outs_p = [], []
+    for e in qev:
+        m = e.queries.shape[0]
+        pdt = np.int32 if e.mode == knn.KNN_VOTE else np.float32
+        outs_s.append((np.empty((m, e.k), np.int32), np.empty((m, e.k), np.float32), np.empty(m, pdt)))
+        outs_p.append((np.empty((m, e.k), np.int32), np.empty((m, e.k), np.float32), np.empty(m, pdt)))
+    h = srv._h
+    tickets = []
+    b0 = srv.stats().batches
+    t_start = time.monotonic_ns()
+    for e, (oi, od, op) in zip(qev, outs_s):
+        tk = ctypes.c_int64()
+        rc = lib.knn_server_submit(h, ids[e.index], e.queries.ctypes.data, e.queries.shape[0], e.k,
+                                   e.mode, oi.ctypes.data, od.ctypes.data, op.ctypes.data,
+                                   ctypes.byref(tk))
+        if rc != 0:
+            raise RuntimeError("submit failed")
+        tickets.append(tk.value)
+    info = knn.knn_ticket_info()
+    t_end = t_start
+    for tk in tickets:
+        lib.knn_server_wait(h, tk, -1, ctypes.byref(info))
+        t_end = max(t_end, info.t_done_ns)
+    served_s = (t_end - t_start) * 1e-9
+    cap_batches = srv.stats().batches - b0
+    launches = knn.knn_kernel_launches() - l0
+    clocks = sampler.stop()
+
+    # plain form: one knn_query per request (host buffers, checked), in order
+    t_start = time.monotonic_ns()
+    for e, (oi, od, op) in zip(qev, outs_p):
+        rc = lib.knn_query(plain_idx[e.index]._h, e.queries.ctypes.data, e.queries.shape[0], e.k,
+                           e.mode, oi.ctypes.data, od.ctypes.data, op.ctypes.data,
+                           knn.KNN_QUERY_CHECKED, None)
+        if rc != 0:
+            raise RuntimeError("plain query failed")
+    plain_s = (time.monotonic_ns() - t_start) * 1e-9
+    identical = all(np.array_equal(a[0], b[0]) and
+                    np.array_equal(a[1].view(np.uint32), b[1].view(np.uint32)) and
+                    np.array_equal(a[2].view(np.uint32), b[2].view(np.uint32))
+                    for a, b in zip(outs_s, outs_p))
+
+    # plain form under the same Poisson arrivals (one request at a time)
+    plat = []
+    base = time.monotonic_ns() + 20_000_000
+    for e, (oi, od, op) in zip(qev, outs_p):
+        sched = base + int(e.t * 1e9)
+        _pace(sched)
+        lib.knn_query(plain_idx[e.index]._h, e.queries.ctypes.data, e.queries.shape[0], e.k,
+                      e.mode, oi.ctypes.data, None, op.ctypes.data, knn.KNN_QUERY_CHECKED, None)
+        plat.append((time.monotonic_ns() - sched) * 1e-6)
+    srv.close()
+
+    cap_served = q_total / served_s
+    cap_plain = q_total / plain_s
+    h2d = sum(e.queries.nbytes for e in qev) / len(qev)
+    d2h = sum(o[0].nbytes + o[1].nbytes + o[2].nbytes for o in outs_s) / len(qev)
+    print(json.dumps({
+        "metric": "queries/sec + p50/p99 latency, continuous-batching server over resident indexes",
+        "value": cap_served, "unit": UNIT, "n_gpus": 1, "steps": len(qev), "warmup": 200,
+        "ms_per_step": served_s * 1e3 / len(qev), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "serving", "indexes": len(specs),
+                   "points": int(sum(ix.n for ix in specs)),
+                   "dims": sorted({ix.d for ix in specs}), "requests": len(qev),
+                   "queries": int(q_total), "ks": [5, 16], "rate_req_s": args.serve_rate,
+                   "seconds": args.serve_seconds, "interleaved_builds": len(bev),
+                   "budget_gb": 60, "resident_gb": round(st0.resident_bytes / 2**30, 2),
+                   "setup_s": round(setup_s, 1), "autotune_s": round(tune_s, 1),
+                   "l2": "inputs (resident indexes, 5.6+ GB) larger than L2"},
+        "poisson": {"offered_req_s": args.serve_rate,
+                    "achieved_qps": q_total / poisson_s,
+                    "window_s": poisson_s,
+                    "p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99), "p999_ms": _pct(lat, 99.9),
+                    "mean_ms": float(np.mean(lat)), "max_submit_lag_ms": float(np.max(lag)),
+                    "batches": len(batches),
+                    "requests_per_batch": len(lat) / max(1, len(batches)),
+                    "builds": {"count": len(bstats),
+                               "ok": sum(1 for b in bstats if b[2] == 0),
+                               "p50_ms": _pct([b[0] for b in bstats], 50),
+                               "max_ms": max([b[0] for b in bstats], default=None),
+                               "admission_wait_max_ms": max([b[1] for b in bstats], default=None),
+                               "drops": int(st1.drops_done)}},
+        "plain": {"capacity_qps": cap_plain, "capacity_req_s": len(qev) / plain_s,
+                  "poisson": {"p50_ms": _pct(plat, 50), "p99_ms": _pct(plat, 99),
+                              "mean_ms": float(np.mean(plat))}},
+        "capacity": {"served_req_s": len(qev) / served_s, "batches": int(cap_batches),
+                     "requests_per_batch": len(qev) / max(1, cap_batches)},
+        "speedup_vs_plain": cap_served / cap_plain,
+        "identical_to_plain": bool(identical),
+        "e2e": {"value": cap_served, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches), "clocks": clocks,
+    }), flush=True)
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         run_reference(args)
     elif args.config == "batched":
         run_batched(args)
+    elif args.config == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

@@ -134,6 +134,14 @@ knn_status knn_server_submit(ghn_server* server, int64_t index_id, const float* 
 knn_status knn_server_wait(ghn_server* server, int64_t ticket, int64_t timeout_us,
                            knn_ticket_info* info);
 
+/*
+ * knn_server_index: the resident index behind an id, for plain calls
+ * (knn_query, knn_index_info) beside the server.  Borrowed: valid until the
+ * index is dropped or the server destroyed; never pass it to knn_free.
+ * KNN_EINVAL when the id is unknown, dropped or not built yet.
+ */
+knn_status knn_server_index(ghn_server* server, int64_t index_id, const ghn_index** index);
+
 /* knn_server_test: knn_server_wait without waiting (*done = 0 or 1). */
 knn_status knn_server_test(ghn_server* server, int64_t ticket, int32_t* done,
                            knn_ticket_info* info);

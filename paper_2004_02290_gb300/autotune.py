@@ -29,11 +29,19 @@ class Choice:
     tried: list  # (width, est_ms)
 
 
-def start_width(points: np.ndarray, k: int) -> float:
-    """A first guess: cells holding about max(2, k/2) points if the data filled its box."""
-    n, d = points.shape
-    span = points.max(axis=0).astype(np.float64) - points.min(axis=0).astype(np.float64)
-    span = np.maximum(span, 1e-12)
+def start_width(points, k: int) -> float:
+    """A first guess: cells holding about max(2, k/2) points if the data filled its box.
+
+    points: n x d numpy array or torch tensor.
+    """
+    n, d = int(points.shape[0]), int(points.shape[1])
+    if hasattr(points, "amin"):  # torch tensor: reduce on its device
+        lo = points.amin(dim=0).double().cpu().numpy()
+        hi = points.amax(dim=0).double().cpu().numpy()
+    else:
+        lo = points.min(axis=0).astype(np.float64)
+        hi = points.max(axis=0).astype(np.float64)
+    span = np.maximum(hi - lo, 1e-12)
     vol = float(np.prod(span))
     occ = max(2.0, k / 2.0)
     return float(np.float32((vol * occ / n) ** (1.0 / d)))
@@ -68,15 +76,27 @@ def tune_width(points, labels, queries, k: int, mode: int, step: float = 0.5,
     import torch
 
     dev = dev or torch.device("cuda:0")
-    pts_h = np.ascontiguousarray(points, np.float32)
-    w0 = start_width(pts_h, k)
-    pts = torch.from_numpy(pts_h).to(dev)
-    lab = torch.from_numpy(np.ascontiguousarray(labels)).to(dev) if labels is not None else None
+
+    def on_dev(a):
+        if a is None:
+            return None
+        if isinstance(a, torch.Tensor):
+            return a.to(dev).contiguous()
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    pts = on_dev(points)
+    if pts.dtype != torch.float32:
+        raise ValueError("points must be float32")
+    w0 = start_width(pts, k)
+    lab = on_dev(labels)
     m = int(queries.shape[0])
     s = min(sample, m)
     rng = np.random.default_rng(0)
     pick = np.sort(rng.choice(m, size=s, replace=False)) if s < m else np.arange(m)
-    q = torch.from_numpy(np.ascontiguousarray(queries[pick], np.float32)).to(dev)
+    if isinstance(queries, torch.Tensor):
+        q = queries.to(dev)[torch.from_numpy(pick).to(dev)].contiguous()
+    else:
+        q = on_dev(np.ascontiguousarray(queries[pick], np.float32))
     stream = torch.cuda.current_stream(dev)
     cache = {}
 

@@ -775,6 +775,23 @@ knn_status knn_server_test(ghn_server* s, int64_t ticket, int32_t* done, knn_tic
     return wait_impl(s, ticket, 0, info, done);
 }
 
+knn_status knn_server_index(ghn_server* s, int64_t index_id, const ghn_index** index)
+{
+    if (!s || !index) {
+        ghn::set_error("knn_server_index: NULL argument");
+        return KNN_EINVAL;
+    }
+    *index = nullptr;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->indexes.find(index_id);
+    if (it == s->indexes.end() || it->second.dropping || !it->second.ready) {
+        set_errf("knn_server_index: index %lld is unknown, dropped or not built", (long long)index_id);
+        return KNN_EINVAL;
+    }
+    *index = it->second.x;
+    return KNN_OK;
+}
+
 knn_status knn_server_stats(ghn_server* s, knn_server_stats_t* out)
 {
     if (!s || !out) {

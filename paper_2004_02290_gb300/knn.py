@@ -47,7 +47,7 @@ EXPORTED = ["knn_batch_build", "knn_batch_info", "knn_batch_query", "knn_batch_p
             "knn_last_error", "knn_abi_version",
             "knn_server_create", "knn_server_build", "knn_server_drop", "knn_server_submit",
             "knn_server_wait", "knn_server_test", "knn_server_stats", "knn_server_clock_ns",
-            "knn_server_build_bytes", "knn_server_destroy"]
+            "knn_server_build_bytes", "knn_server_index", "knn_server_destroy"]
 
 
 class knn_server_config(ctypes.Structure):
@@ -146,6 +146,8 @@ def library(path: str | None = None) -> ctypes.CDLL:
         lib.knn_server_stats.restype = i32
         lib.knn_server_clock_ns.argtypes = []
         lib.knn_server_clock_ns.restype = i64
+        lib.knn_server_index.argtypes = [vp, i64, ctypes.POINTER(vp)]
+        lib.knn_server_index.restype = i32
         lib.knn_server_build_bytes.argtypes = [i64, i32, i32]
         lib.knn_server_build_bytes.restype = i64
         lib.knn_server_destroy.argtypes = [vp]
@@ -545,6 +547,14 @@ class Server:
             self._keep.pop(ticket, None)
         return info
 
+    def index(self, index_id: int) -> "Index":
+        """The resident index behind an id, for plain queries (borrowed: never free it)."""
+        h = ctypes.c_void_p()
+        _check(library().knn_server_index(self._h, index_id, ctypes.byref(h)))
+        info = knn_index_info_t()
+        _check(library().knn_index_info(h, ctypes.byref(info)))
+        return _Borrowed(h, int(info.n), int(info.d))
+
     def stats(self) -> knn_server_stats_t:
         s = knn_server_stats_t()
         _check(library().knn_server_stats(self._h, ctypes.byref(s)))
@@ -561,6 +571,16 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+class _Borrowed(Index):
+    """An index owned by a server: queries work, freeing is the server's job."""
+
+    def free(self):
+        self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        pass
 
 
 def knn_server_build_bytes(n: int, d: int, labels: bool) -> int:

@@ -230,3 +230,125 @@ def gen_batched(count=256, seed=3, n_lo=1_000, n_hi=2_000_000, dims=(2, 3, 4, 6)
         out.append(Workload(name=f"batched[{i}]", points=x, labels=lab, queries=q, k=k,
                             mode=mode, w=float("nan"), table=TABLE_AUTO, seed=seed))
     return out
+
+
+# ---- the serving workload: resident indexes and a Poisson request stream ----
+
+@dataclasses.dataclass
+class ServeIndex:
+    """One index of the serving workload: a Gaussian mixture, drawn on demand."""
+    n: int
+    d: int
+    mode: int             # VOTE (label = cluster) or MEAN (smooth target + noise)
+    centres: np.ndarray   # ncl x d, float64
+    sigma: float
+    seed: int
+
+
+@dataclasses.dataclass
+class ServeEvent:
+    t: float              # arrival, seconds from the start
+    kind: str             # "query" or "build"
+    index: int = -1       # query: position in the resident list
+    queries: np.ndarray | None = None
+    k: int = 0
+    mode: int = -1
+    spec: ServeIndex | None = None  # build: the new index
+
+
+def _serve_index(rng, n, d, seed):
+    ncl = int(rng.integers(4, 33))
+    return ServeIndex(n=n, d=d, mode=VOTE if seed % 2 == 0 else MEAN,
+                      centres=rng.random((ncl, d)), sigma=float(rng.uniform(0.02, 0.1)),
+                      seed=seed)
+
+
+def gen_serving_indexes(count=64, seed=5, n_lo=10_000, n_hi=50_000_000, dims=(2, 3, 4, 5, 6),
+                        cap_bytes=60 << 30, bytes_per_point=72):
+    """Resident indexes of the serving workload.
+
+    n log-uniform in [n_lo, n_hi], d uniform in `dims`, 4..32 clusters with
+    centres uniform in [0,1]^d and one sigma uniform in [0.02, 0.1]; even
+    positions classify, odd ones regress.  When the indexes would hold more
+    than cap_bytes (at bytes_per_point per point, an over-estimate of the
+    resident size), every n is scaled down by the same factor.
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(round(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi)))))
+        d = int(rng.choice(dims))
+        out.append(_serve_index(rng, n, d, seed * 1000 + i))
+    total = sum(ix.n for ix in out) * bytes_per_point
+    if total > cap_bytes:
+        f = cap_bytes / total
+        for ix in out:
+            ix.n = max(n_lo, int(ix.n * f))
+    return out
+
+
+def serving_points(ix: ServeIndex, device):
+    """(points n x d float32, labels) of an index, drawn on `device` from a seeded torch stream."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(ix.seed)
+    c = torch.from_numpy(ix.centres).to(device=device, dtype=torch.float64)
+    comp = torch.randint(0, c.shape[0], (ix.n,), generator=g, device=device)
+    x = c[comp] + ix.sigma * torch.randn((ix.n, ix.d), generator=g, device=device,
+                                         dtype=torch.float64)
+    pts = x.to(torch.float32).contiguous()
+    if ix.mode == VOTE:
+        lab = comp.to(torch.int32)
+    else:
+        xd = pts.to(torch.float64)
+        y = torch.sin(3.0 * xd[:, 0]) + 0.5 * xd.sum(dim=1) + 0.05 * torch.randn(
+            ix.n, generator=g, device=device, dtype=torch.float64)
+        lab = y.to(torch.float32)
+    del x, comp
+    return pts, lab.contiguous()
+
+
+def serving_queries(ix: ServeIndex, m: int, rng) -> np.ndarray:
+    """m queries from an index's mixture (host, float32)."""
+    comp = rng.integers(0, ix.centres.shape[0], size=m)
+    return _f32(ix.centres[comp] + ix.sigma * rng.standard_normal((m, ix.d)))
+
+
+def gen_serving_requests(indexes, rate=2000.0, duration=10.0, seed=6, m_lo=1, m_hi=4096,
+                         ks=(5, 16), build_rate=4.0, build_n=(10_000, 5_000_000),
+                         dims=(2, 3, 4, 5, 6)):
+    """Poisson arrivals over `duration` seconds.
+
+    Query requests arrive at `rate` per second; each names a resident index
+    uniformly, has m log-uniform in [m_lo, m_hi] queries from that index's
+    mixture and k uniform in `ks`, with the index's own head.  Build requests
+    arrive at `build_rate` per second, each for a new index with n
+    log-uniform in `build_n`.
+    """
+    rng = np.random.default_rng(seed)
+    events = []
+    t = 0.0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= duration:
+            break
+        i = int(rng.integers(0, len(indexes)))
+        ix = indexes[i]
+        m = int(np.exp(rng.uniform(np.log(m_lo), np.log(m_hi + 1))))
+        m = min(max(m, m_lo), m_hi)
+        events.append(ServeEvent(t=t, kind="query", index=i, queries=serving_queries(ix, m, rng),
+                                 k=int(rng.choice(ks)), mode=ix.mode))
+    t = 0.0
+    j = 0
+    while build_rate > 0:
+        t += rng.exponential(1.0 / build_rate)
+        if t >= duration:
+            break
+        n = int(round(np.exp(rng.uniform(np.log(build_n[0]), np.log(build_n[1])))))
+        events.append(ServeEvent(t=t, kind="build",
+                                 spec=_serve_index(rng, n, int(rng.choice(dims)),
+                                                   seed * 100000 + j)))
+        j += 1
+    events.sort(key=lambda e: e.t)
+    return events

@@ -214,3 +214,19 @@ def test_drop_waits_for_earlier_requests(server_with_indexes):
     assert info.t_done_ns >= max(i.t_done_ns for i in done)
     for r in reqs[1:]:
         assert np.array_equal(r[1], reqs[0][1])
+
+
+def test_borrowed_index_answers_plain_queries(server_with_indexes):
+    srv, ids_of, data = server_with_indexes
+    idx = srv.index(ids_of[2])
+    q = np.random.default_rng(9).random((40, 4)).astype(np.float32)
+    t, ids, d2, pred = srv.submit(ids_of[2], q, 11, knn.KNN_MEDIAN)
+    assert srv.wait(t).status == knn.KNN_OK
+    p_ids, p_d2, p_pred = idx.query(q, 11, knn.KNN_MEDIAN, flags=knn.KNN_QUERY_CHECKED)
+    _same((ids, d2, pred), (np.asarray(p_ids), np.asarray(p_d2), np.asarray(p_pred)))
+    idx.free()  # a no-op for a borrowed index: the server still owns it
+    t, ids2, _, _ = srv.submit(ids_of[2], q, 11, knn.KNN_MEDIAN)
+    assert srv.wait(t).status == knn.KNN_OK
+    assert np.array_equal(ids, ids2)
+    with pytest.raises(knn.KnnError):
+        srv.index(987654)
