@@ -6,10 +6,14 @@ path (the CUDA library and its binding) never does.  Nothing here is shared
 with the CUDA library.
 """
 from .oracle import (  # noqa: F401
+    RULE_EXACT,
+    RULE_NONE,
+    RULE_PAPER,
     Grid,
     brute_force,
     build_library,
     count_cells,
     library,
+    measure_cells,
     shell_count,
 )

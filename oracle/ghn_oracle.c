@@ -23,7 +23,19 @@
  * Readings of points the paper leaves open (each is listed with its reason in
  * the design notes of the repository):
  *   origin    per-dimension minimum of the training points (splits cover the
- *             range of values, Sec. III.A); one scalar width w for all dims.
+ *             range of values, Sec. III.A).
+ *   widths    one cell measurement w_j per dimension (Sec. III.A: cells are
+ *             identical but not necessarily equilateral); a scalar width is
+ *             the case w_j = w for every j.
+ *   splits    when a grid comes from the paper's cell measurement (s_j equal
+ *             splits of each range, the last one closed), training cells are
+ *             clamped to s_j - 1 so that the maximum lies in the last split;
+ *             queries are not clamped to the splits.
+ *   measure   per dimension, the largest s (at most 2^21) for which every
+ *             one of the s splits holds a training point, a point's split
+ *             being its Eq. 1 coordinate with w = r / s (r = max - min, single
+ *             precision) clamped to s - 1; a dimension with r = 0 gets s = 1
+ *             and w = 1.
  *   key       t = (p_j - o_j) / w in IEEE single precision, round to nearest,
  *             c_j = floor(t); a query clamps floor(t) to [-2^40, 2^40].
  *   layer L   the cells whose Chebyshev distance to the central cell is L
@@ -35,6 +47,11 @@
  *   stop      after layer L, when the buffer holds k points and layer L made
  *             no update, or when cube(L) covers the whole box (every later
  *             layer is empty, so the result cannot change).
+ *   exact     (a certified variant of the stop, not the paper's rule): after
+ *             layer L, stop when the buffer holds k points and the k-th
+ *             squared distance is below the squared distance from the query
+ *             to every cell outside cube(L) that the box can hold, less
+ *             rounding margins; the result then equals exhaustive KNN.
  *   order     (squared distance, training index) ascending; squared distance
  *             in single precision, dimension order, no fused multiply-add
  *             (compile with -ffp-contract=off).
@@ -67,7 +84,8 @@ typedef struct {
 
 typedef struct {
     int32_t d;
-    float w;
+    float w[GHN_ORACLE_MAXD];       /* cell measurement per dimension */
+    int64_t split[GHN_ORACLE_MAXD]; /* training cells clamped to split - 1 (0: no clamp) */
     int64_t n;
     float origin[GHN_ORACLE_MAXD];
     int64_t cmax[GHN_ORACLE_MAXD]; /* largest cell coordinate per dimension */
@@ -111,12 +129,14 @@ static int64_t find_cell(const ghn_oracle* g, const int64_t* c)
     return -1;
 }
 
-/* Eq. 1 for a training point: c_j = floor((p_j - o_j) / w), single precision. */
+/* Eq. 1 for a training point: c_j = floor((p_j - o_j) / w_j), single
+   precision; clamped into the last split when the grid has splits. */
 static void training_cell(const ghn_oracle* g, const float* p, int64_t* c)
 {
     for (int32_t j = 0; j < g->d; ++j) {
-        float t = (p[j] - g->origin[j]) / g->w;
+        float t = (p[j] - g->origin[j]) / g->w[j];
         c[j] = (int64_t)floorf(t);
+        if (g->split[j] > 0 && c[j] > g->split[j] - 1) c[j] = g->split[j] - 1;
     }
 }
 
@@ -124,7 +144,7 @@ static void training_cell(const ghn_oracle* g, const float* p, int64_t* c)
 static void query_cell(const ghn_oracle* g, const float* q, int64_t* c)
 {
     for (int32_t j = 0; j < g->d; ++j) {
-        float t = floorf((q[j] - g->origin[j]) / g->w);
+        float t = floorf((q[j] - g->origin[j]) / g->w[j]);
         if (t < -GHN_ORACLE_QCLAMP) t = -GHN_ORACLE_QCLAMP;
         if (t > GHN_ORACLE_QCLAMP) t = GHN_ORACLE_QCLAMP;
         c[j] = (int64_t)t;
@@ -166,22 +186,31 @@ void oracle_free(ghn_oracle* g)
 
 /*
  * Cell sampling (Algorithm 1).  points: n*d row-major floats; labels: n
- * 32-bit outputs (int32 classes or float targets, kept as raw bits) or NULL.
- * Returns 0 on success, 1 on bad arguments (n < 1, d outside 1..8, w not a
- * positive finite number, a non-finite coordinate), 2 when out of memory.
+ * 32-bit outputs (int32 classes or float targets, kept as raw bits) or NULL;
+ * widths: d cell measurements; splits: d split counts (training cells are
+ * clamped to split - 1) or NULL.  Returns 0 on success, 1 on bad arguments
+ * (n < 1, d outside 1..8, a width not a positive finite number, a split
+ * below 1, a non-finite coordinate), 2 when out of memory.
  */
-int oracle_build(const float* points, const uint32_t* labels, int64_t n, int32_t d, float w,
-                 ghn_oracle** out)
+int oracle_build_grid(const float* points, const uint32_t* labels, int64_t n, int32_t d,
+                      const float* widths, const int64_t* splits, ghn_oracle** out)
 {
     *out = NULL;
-    if (n < 1 || d < 1 || d > GHN_ORACLE_MAXD || !(w > 0.0f) || !isfinite(w)) return 1;
+    if (n < 1 || d < 1 || d > GHN_ORACLE_MAXD) return 1;
+    for (int32_t j = 0; j < d; ++j) {
+        if (!(widths[j] > 0.0f) || !isfinite(widths[j])) return 1;
+        if (splits && splits[j] < 1) return 1;
+    }
     for (int64_t i = 0; i < n * d; ++i)
         if (!isfinite(points[i])) return 1;
 
     ghn_oracle* g = (ghn_oracle*)calloc(1, sizeof(ghn_oracle));
     if (!g) return 2;
     g->d = d;
-    g->w = w;
+    for (int32_t j = 0; j < d; ++j) {
+        g->w[j] = widths[j];
+        g->split[j] = splits ? splits[j] : 0;
+    }
     g->n = n;
     g->points = (float*)malloc(sizeof(float) * (size_t)(n * d));
     g->cellcap = 1024;
@@ -207,7 +236,7 @@ int oracle_build(const float* points, const uint32_t* labels, int64_t n, int32_t
         g->origin[j] = lo;
         g->cmax[j] = 0;
         /* refuse grids whose cell coordinates would not fit an int64 */
-        if (!((hi - lo) / w < 4611686018427387904.0f)) {
+        if (!((hi - lo) / widths[j] < 4611686018427387904.0f)) {
             oracle_free(g);
             return 1;
         }
@@ -247,6 +276,86 @@ int oracle_build(const float* points, const uint32_t* labels, int64_t n, int32_t
     }
     *out = g;
     return 0;
+}
+
+/* ---- the cell measurement of Sec. III.A ---- */
+
+static int cmp_float(const void* a, const void* b)
+{
+    float x = *(const float*)a, y = *(const float*)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+/* Split of value v among s splits of width w from lo (Eq. 1, the last split closed). */
+static int64_t split_of(float v, float lo, float w, int64_t s)
+{
+    float t = floorf((v - lo) / w);
+    if (!(t < (float)s)) return s - 1;
+    return (int64_t)t;
+}
+
+#define GHN_ORACLE_MAX_SPLITS 2097152 /* 2^21 */
+
+/*
+ * Per dimension, the largest number of equal splits of the range of values
+ * such that every split holds at least one training point (Sec. III.A, the
+ * "cell measurements"); the width is range / splits.  Candidates go from
+ * min(distinct values, 2^21) down; the first one whose splits are all
+ * occupied wins (a split is occupied when some value lands in it; the values
+ * are visited in increasing order, so it suffices that consecutive distinct
+ * values never skip a split and that the largest lands in the last one).
+ * splits, widths: d entries each.  Returns 0, 1 on bad arguments, 2 when out
+ * of memory.
+ */
+int oracle_measure(const float* points, int64_t n, int32_t d, int64_t* splits, float* widths)
+{
+    if (n < 1 || d < 1 || d > GHN_ORACLE_MAXD) return 1;
+    for (int64_t i = 0; i < n * d; ++i)
+        if (!isfinite(points[i])) return 1;
+    float* v = (float*)malloc(sizeof(float) * (size_t)n);
+    if (!v) return 2;
+    for (int32_t j = 0; j < d; ++j) {
+        for (int64_t i = 0; i < n; ++i) v[i] = points[i * d + j];
+        qsort(v, (size_t)n, sizeof(float), cmp_float);
+        int64_t u = 0; /* distinct values, in place */
+        for (int64_t i = 0; i < n; ++i)
+            if (u == 0 || v[i] != v[u - 1]) v[u++] = v[i];
+        float lo = v[0], r = v[u - 1] - v[0];
+        splits[j] = 1;
+        widths[j] = 1.0f;
+        if (!(r > 0.0f)) continue; /* one value: one split */
+        int64_t s = u < GHN_ORACLE_MAX_SPLITS ? u : GHN_ORACLE_MAX_SPLITS;
+        for (; s >= 1; --s) {
+            float w = r / (float)s;
+            if (!(w > 0.0f)) continue;
+            int ok = split_of(v[u - 1], lo, w, s) == s - 1;
+            int64_t prev = split_of(v[0], lo, w, s);
+            ok = ok && prev == 0;
+            for (int64_t i = 1; ok && i < u; ++i) {
+                int64_t c = split_of(v[i], lo, w, s);
+                if (c - prev > 1) ok = 0;
+                prev = c;
+            }
+            if (ok) {
+                splits[j] = s;
+                widths[j] = w;
+                break;
+            }
+        }
+    }
+    free(v);
+    return 0;
+}
+
+/* Cell sampling with one width w for every dimension and no splits. */
+int oracle_build(const float* points, const uint32_t* labels, int64_t n, int32_t d, float w,
+                 ghn_oracle** out)
+{
+    float widths[GHN_ORACLE_MAXD];
+    *out = NULL;
+    if (d < 1 || d > GHN_ORACLE_MAXD) return 1;
+    for (int32_t j = 0; j < d; ++j) widths[j] = w;
+    return oracle_build_grid(points, labels, n, d, widths, NULL, out);
 }
 
 /* ---- the k-bounded buffer (kept sorted by (distance, index)) ---- */
@@ -406,13 +515,48 @@ static float median_of(const ghn_oracle* g, const oracle_entry* buf, int32_t siz
 }
 
 /*
+ * The certified stop: after cube(L) has been visited, can a point outside it
+ * still enter a full buffer whose k-th squared distance is kth?  A training
+ * point in a cell beyond c0_j + L along axis j lies at or above
+ * o_j + (c0_j + L + 1) w_j, less the rounding of Eq. 1 (at most a relative
+ * 2^-23 of the quotient, taken here as 2^-21); below c0_j - L it lies under
+ * o_j + (c0_j - L) w_j plus that margin.  Sides where the box holds no cell
+ * beyond cube(L) do not count.  The smallest such gap bounds the distance of
+ * every point not yet seen; its single-precision squared distance is at least
+ * gap^2 (1 - 2^-20) (d + 2 roundings of 2^-24 each).  Stop when kth is below
+ * that.
+ */
+static int certified(const ghn_oracle* g, const float* q, const int64_t* c0, int64_t L, float kth)
+{
+    double gap = INFINITY;
+    for (int32_t j = 0; j < g->d; ++j) {
+        double w = (double)g->w[j], o = (double)g->origin[j], qj = (double)q[j];
+        if (c0[j] + L < g->cmax[j]) {
+            double cu = (double)(c0[j] + L + 1);
+            double edge = o + cu * w - fabs(cu) * w * 0x1p-21;
+            double up = edge - qj;
+            if (up < gap) gap = up;
+        }
+        if (c0[j] - L > 0) {
+            double cl = (double)(c0[j] - L);
+            double edge = o + cl * w + fabs(cl) * w * 0x1p-21;
+            double down = qj - edge;
+            if (down < gap) gap = down;
+        }
+    }
+    if (!(gap > 0.0)) return 0;
+    return (double)kth < gap * gap * (1.0 - 0x1p-20);
+}
+
+/*
  * Predict one query.  ids[k] / dist2[k] receive the neighbours in
  * (distance, index) order, padded with -1 / +inf.  mode 0 = vote (labels read
  * as int32, pred is int32), mode 1 = mean and mode 2 = median (labels read as
  * float, pred is float), mode -1 = no prediction.  stats (may be NULL) receives
  * {layers visited (L* + 1), occupied cells looked up, points examined}.
- * stop_rule = 0 disables the paper's stop rule (the walk then ends only when
- * the cube covers the box: exhaustive search), for tests.
+ * stop_rule: 1 the paper's rule (Sec. III.B); 2 the certified stop (the
+ * result equals exhaustive KNN); 0 no stop rule (the walk ends only when the
+ * cube covers the box: exhaustive search).
  * Returns 0, or 1 on bad arguments.
  */
 int oracle_query_ex(const ghn_oracle* g, const float* q, int32_t k, int32_t mode, int32_t stop_rule,
@@ -456,7 +600,8 @@ int oracle_query_ex(const ghn_oracle* g, const float* q, int32_t k, int32_t mode
         }
         x.updated = 0;
         for_each_shell_cell(d, c0, L, lo, hi, visit_cell, &x);
-        if (stop_rule && x.size == k && !x.updated) break;
+        if (stop_rule == 1 && x.size == k && !x.updated) break;
+        if (stop_rule == 2 && x.size == k && certified(g, q, c0, L, buf[k - 1].dist)) break;
         if (covers) break;
     }
 
@@ -498,17 +643,25 @@ int oracle_query_ex(const ghn_oracle* g, const float* q, int32_t k, int32_t mode
     return 0;
 }
 
-/* A batch of m queries (q is m*d), outputs m*k / m, stats m*3 (may be NULL). */
-int oracle_query(const ghn_oracle* g, const float* q, int64_t m, int32_t k, int32_t mode,
-                 int32_t* ids, float* dist2, void* pred, int64_t* stats)
+/* A batch of m queries (q is m*d) under a stop rule (as oracle_query_ex);
+   outputs m*k / m, stats m*3 (may be NULL). */
+int oracle_query_rule(const ghn_oracle* g, const float* q, int64_t m, int32_t k, int32_t mode,
+                      int32_t stop_rule, int32_t* ids, float* dist2, void* pred, int64_t* stats)
 {
     for (int64_t i = 0; i < m; ++i) {
         void* p = pred ? (void*)((uint32_t*)pred + i) : NULL;
-        int rc = oracle_query_ex(g, q + i * g->d, k, mode, 1, ids + i * k, dist2 + i * k,
+        int rc = oracle_query_ex(g, q + i * g->d, k, mode, stop_rule, ids + i * k, dist2 + i * k,
                                  mode >= 0 ? p : NULL, stats ? stats + 3 * i : NULL);
         if (rc) return rc;
     }
     return 0;
+}
+
+/* A batch of m queries under the paper's stop rule. */
+int oracle_query(const ghn_oracle* g, const float* q, int64_t m, int32_t k, int32_t mode,
+                 int32_t* ids, float* dist2, void* pred, int64_t* stats)
+{
+    return oracle_query_rule(g, q, m, k, mode, 1, ids, dist2, pred, stats);
 }
 
 /* ---- original KNN (Sec. I): scan everything, then sort ---- */

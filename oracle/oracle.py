@@ -57,6 +57,15 @@ def library() -> ctypes.CDLL:
             lib.oracle_build.argtypes = [_f32p, _u32p, ctypes.c_int64, ctypes.c_int32,
                                          ctypes.c_float, ctypes.POINTER(vp)]
             lib.oracle_build.restype = ctypes.c_int
+            lib.oracle_build_grid.argtypes = [_f32p, _u32p, ctypes.c_int64, ctypes.c_int32,
+                                              _f32p, _i64p, ctypes.POINTER(vp)]
+            lib.oracle_build_grid.restype = ctypes.c_int
+            lib.oracle_measure.argtypes = [_f32p, ctypes.c_int64, ctypes.c_int32, _i64p, _f32p]
+            lib.oracle_measure.restype = ctypes.c_int
+            lib.oracle_query_rule.argtypes = [vp, _f32p, ctypes.c_int64, ctypes.c_int32,
+                                              ctypes.c_int32, ctypes.c_int32, _i32p, _f32p, vp,
+                                              _i64p]
+            lib.oracle_query_rule.restype = ctypes.c_int
             lib.oracle_free.argtypes = [vp]
             lib.oracle_free.restype = None
             lib.oracle_query.argtypes = [vp, _f32p, ctypes.c_int64, ctypes.c_int32,
@@ -93,16 +102,43 @@ def _ptr(a: np.ndarray, t):
     return a.ctypes.data_as(t)
 
 
-class Grid:
-    """The oracle's grid (Algorithm 1) over training points with 32-bit outputs."""
+RULE_NONE, RULE_PAPER, RULE_EXACT = 0, 1, 2
 
-    def __init__(self, points, labels, w: float):
+
+def measure_cells(points):
+    """The paper's cell measurement (Sec. III.A): (splits int64[d], widths float32[d])."""
+    pts = _f32(points)
+    n, d = pts.shape
+    splits = np.zeros(d, np.int64)
+    widths = np.zeros(d, np.float32)
+    rc = library().oracle_measure(_ptr(pts, _f32p), n, d, _ptr(splits, _i64p),
+                                  _ptr(widths, _f32p))
+    if rc != 0:
+        raise ValueError(f"oracle_measure failed with code {rc}")
+    return splits, widths
+
+
+class Grid:
+    """The oracle's grid (Algorithm 1) over training points with 32-bit outputs.
+
+    w: one width, or d widths (one per dimension); splits: d split counts
+    (training cells clamped to split - 1, the grid of the cell measurement)
+    or None.
+    """
+
+    def __init__(self, points, labels, w, splits=None):
         lib = library()
         pts = _f32(points)
         if pts.ndim != 2:
             raise ValueError("points must be n x d")
         self.n, self.d = pts.shape
-        self.w = np.float32(w)
+        wv = np.asarray(w, np.float32)
+        self.widths = np.ascontiguousarray(np.broadcast_to(wv, (self.d,)) if wv.ndim == 0 else wv,
+                                           np.float32)
+        if self.widths.shape != (self.d,):
+            raise ValueError("w must be a scalar or d widths")
+        self.w = self.widths[0] if wv.ndim == 0 else self.widths
+        self.splits = None if splits is None else np.ascontiguousarray(splits, np.int64)
         self._labels = None
         lab_p = None
         if labels is not None:
@@ -112,8 +148,10 @@ class Grid:
             self._labels = lab
             lab_p = _ptr(lab.view(np.uint32), _u32p)
         h = ctypes.c_void_p()
-        rc = lib.oracle_build(_ptr(pts, _f32p), lab_p, self.n, self.d, ctypes.c_float(self.w),
-                              ctypes.byref(h))
+        rc = lib.oracle_build_grid(_ptr(pts, _f32p), lab_p, self.n, self.d,
+                                   _ptr(self.widths, _f32p),
+                                   _ptr(self.splits, _i64p) if self.splits is not None else None,
+                                   ctypes.byref(h))
         if rc != 0:
             raise ValueError(f"oracle_build failed with code {rc}")
         self._h = h
@@ -158,10 +196,11 @@ class Grid:
                                   _ptr(c, _i64p))
         return c
 
-    def query(self, queries, k: int, mode: int = -1, stats: bool = False):
+    def query(self, queries, k: int, mode: int = -1, stats: bool = False, rule: int = RULE_PAPER):
         """Neighbours of each query: (ids m x k, dist2 m x k, pred m or None[, stats m x 3]).
 
         mode: 0 vote (int32 outputs), 1 mean, 2 median (float outputs), -1 none.
+        rule: RULE_PAPER (Sec. III.B), RULE_EXACT (certified stop), RULE_NONE.
         """
         q = _f32(queries).reshape(-1, self.d)
         m = q.shape[0]
@@ -173,11 +212,11 @@ class Grid:
         elif mode in (1, 2):
             pred = np.zeros(m, np.float32)
         st = np.zeros((m, 3), np.int64) if stats else None
-        rc = self._lib.oracle_query(self._h, _ptr(q, _f32p), m, k, mode, _ptr(ids, _i32p),
-                                    _ptr(d2, _f32p),
-                                    pred.ctypes.data_as(ctypes.c_void_p) if pred is not None
-                                    else None,
-                                    _ptr(st, _i64p) if st is not None else None)
+        rc = self._lib.oracle_query_rule(self._h, _ptr(q, _f32p), m, k, mode, rule,
+                                         _ptr(ids, _i32p), _ptr(d2, _f32p),
+                                         pred.ctypes.data_as(ctypes.c_void_p)
+                                         if pred is not None else None,
+                                         _ptr(st, _i64p) if st is not None else None)
         if rc != 0:
             raise ValueError(f"oracle_query failed with code {rc}")
         return (ids, d2, pred, st) if stats else (ids, d2, pred)

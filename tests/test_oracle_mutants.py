@@ -22,12 +22,26 @@ SRC = os.path.join(ROOT, "oracle", "ghn_oracle.c")
 # the walk at layer 0 instead of the first layer that reaches the box (the
 # skipped layers are empty, so the buffer and the stop test are unchanged).
 MUTANTS = [
-    ("trunc_instead_of_floor_query", "float t = floorf((q[j] - g->origin[j]) / g->w);",
-     "float t = truncf((q[j] - g->origin[j]) / g->w);"),
-    ("origin_sign", "float t = (p[j] - g->origin[j]) / g->w;",
-     "float t = (p[j] + g->origin[j]) / g->w;"),
-    ("double_precision_key", "float t = (p[j] - g->origin[j]) / g->w;\n        c[j] = (int64_t)floorf(t);",
-     "double t = ((double)p[j] - (double)g->origin[j]) / (double)g->w;\n        c[j] = (int64_t)floor(t);"),
+    ("trunc_instead_of_floor_query", "float t = floorf((q[j] - g->origin[j]) / g->w[j]);",
+     "float t = truncf((q[j] - g->origin[j]) / g->w[j]);"),
+    ("origin_sign", "float t = (p[j] - g->origin[j]) / g->w[j];",
+     "float t = (p[j] + g->origin[j]) / g->w[j];"),
+    ("double_precision_key", "float t = (p[j] - g->origin[j]) / g->w[j];\n        c[j] = (int64_t)floorf(t);",
+     "double t = ((double)p[j] - (double)g->origin[j]) / (double)g->w[j];\n        c[j] = (int64_t)floor(t);"),
+    ("width_of_first_dimension", "float t = (p[j] - g->origin[j]) / g->w[j];",
+     "float t = (p[j] - g->origin[j]) / g->w[0];"),
+    ("no_split_clamp", "if (g->split[j] > 0 && c[j] > g->split[j] - 1) c[j] = g->split[j] - 1;",
+     "(void)0;"),
+    ("measure_misses_top", "int64_t s = u < GHN_ORACLE_MAX_SPLITS ? u : GHN_ORACLE_MAX_SPLITS;",
+     "int64_t s = (u < GHN_ORACLE_MAX_SPLITS ? u : GHN_ORACLE_MAX_SPLITS) - 1;"),
+    ("measure_skip_allowed", "if (c - prev > 1) ok = 0;", "if (c - prev > 2) ok = 0;"),
+    ("measure_no_last_split_clamp", "if (!(t < (float)s)) return s - 1;",
+     "if (!(t < (float)s + 1.0f)) return s;"),
+    ("certified_edge_off_by_one", "double cu = (double)(c0[j] + L + 1);",
+     "double cu = (double)(c0[j] + L + 2);"),
+    ("certified_ignores_box", "if (c0[j] + L < g->cmax[j]) {", "if (1) {"),
+    ("certified_without_full_buffer", "if (stop_rule == 2 && x.size == k && certified(",
+     "if (stop_rule == 2 && certified("),
     ("origin_is_max", "if (points[i * d + j] < lo) lo = points[i * d + j];",
      "if (points[i * d + j] > lo) lo = points[i * d + j];"),
     ("dropped_distance_term", "acc = acc + s;", "acc = s;"),
@@ -37,10 +51,10 @@ MUTANTS = [
      "return da > db || (da == db && ia < ib);"),
     ("tie_break_flipped", "return da < db || (da == db && ia < ib);",
      "return da < db || (da == db && ia > ib);"),
-    ("stop_without_full_buffer", "if (stop_rule && x.size == k && !x.updated) break;",
-     "if (stop_rule && !x.updated) break;"),
-    ("stop_after_update", "if (stop_rule && x.size == k && !x.updated) break;",
-     "if (stop_rule && x.size == k) break;"),
+    ("stop_without_full_buffer", "if (stop_rule == 1 && x.size == k && !x.updated) break;",
+     "if (stop_rule == 1 && !x.updated) break;"),
+    ("stop_after_update", "if (stop_rule == 1 && x.size == k && !x.updated) break;",
+     "if (stop_rule == 1 && x.size == k) break;"),
     ("shell_includes_inside", "if (cheb == L) {", "if (cheb <= L) {"),
     ("covers_off_by_one", "if (c0[j] - L > 0 || c0[j] + L < g->cmax[j]) covers = 0;",
      "if (c0[j] - L > 1 || c0[j] + L < g->cmax[j]) covers = 0;"),
@@ -55,8 +69,9 @@ MUTANTS = [
     ("layers_count", "stats[0] = L + 1;", "stats[0] = L;"),
     ("median_upper_middle", "out = (float)(((double)v[size / 2 - 1] + (double)v[size / 2]) / 2.0);",
      "out = v[size / 2];"),
-    ("median_natural_order", "return x < y ? -1 : (x > y ? 1 : 0);",
-     "float fa = *(const float*)a, fb = *(const float*)b;\n    (void)x; (void)y;\n    return fa < fb ? -1 : (fa > fb ? 1 : 0);"),
+    ("median_natural_order",
+     "uint32_t x = total_order_key(*(const float*)a), y = total_order_key(*(const float*)b);",
+     "float x = *(const float*)a, y = *(const float*)b;"),
     ("median_sum_in_single", "out = (float)(((double)v[size / 2 - 1] + (double)v[size / 2]) / 2.0);",
      "out = (v[size / 2 - 1] + v[size / 2]) / 2.0f;"),
     ("buffer_keeps_k_plus", "if (*size == k && !entry_less(dist, id, buf[k - 1].dist, buf[k - 1].id)) return 0;",

@@ -375,3 +375,131 @@ def test_median_with_fewer_points_than_k_and_none():
     q = np.array([[0.0]], np.float32)
     _, _, pred = _one_dim_grid([4.0, 1.0, 9.0]).query(q, 6, 2)
     assert pred[0] == np.float32(4.0)
+
+
+# ---- per-dimension widths, the cell measurement, the certified stop ----
+
+def test_per_dimension_eq1_cells():
+    gold = _golden("per_dim_cells.json")
+    pts = np.array(gold["points"], np.float32)
+    g = oracle.Grid(pts, None, np.array(gold["widths"], np.float32))
+    assert g.cells_of(pts).tolist() == gold["cells"]
+
+
+def _measure_brute(v):
+    """Largest s whose s equal splits (Eq. 1 cells clamped to s - 1) are all occupied."""
+    v = np.asarray(v, np.float32)
+    lo = v.min()
+    r = np.float32(v.max() - lo)
+    if r == 0:
+        return 1, np.float32(1.0)
+    best = (1, r)
+    for s in range(1, len(np.unique(v)) + 1):
+        w = np.float32(r / np.float32(s))
+        c = np.minimum(np.floor((v - lo) / w), s - 1).astype(np.int64)
+        if set(c.tolist()) == set(range(s)):
+            best = (s, w)
+    return best
+
+
+def test_measure_hand_examples():
+    # 0..9: ten splits of width 0.9 (s = 11 leaves split 5 empty)
+    x = np.arange(10, dtype=np.float32)
+    # {0, 1, 3}: three splits of width 1 (3 lands in the closed last split)
+    y = np.array([0, 1, 3, 0, 1, 3, 0, 1, 3, 0], np.float32)
+    # {0, 1, 2, 10}: s = 4 (width 2.5) and s = 3 leave middle splits empty; s = 2
+    z = np.array([0, 1, 2, 10, 0, 1, 2, 10, 0, 1], np.float32)
+    splits, widths = oracle.measure_cells(np.stack([x, y, z], axis=1))
+    assert splits.tolist() == [10, 3, 2]
+    assert widths.tolist() == [np.float32(0.9), 1.0, 5.0]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_measure_is_the_largest_full_split_brute_force(seed):
+    rng = np.random.default_rng(seed)
+    n, d = int(rng.integers(5, 120)), int(rng.integers(1, 4))
+    if seed % 3 == 0:
+        x = rng.random((n, d))
+    elif seed % 3 == 1:
+        x = np.round(rng.normal(0.5, 0.2, (n, d)) * 20) / 20  # ties and gaps
+    else:
+        x = np.concatenate([rng.normal(0.2, 0.01, (n, d)), rng.normal(0.9, 0.05, (5, d))])
+    x = x.astype(np.float32)
+    splits, widths = oracle.measure_cells(x)
+    for j in range(x.shape[1]):
+        s, w = _measure_brute(x[:, j])
+        assert splits[j] == s and widths[j] == w, (j, splits[j], s)
+
+
+def test_measured_grid_occupies_every_split():
+    x, _, _ = wl.uniform(400, 1, 3, seed=77)
+    splits, widths = oracle.measure_cells(x)
+    g = oracle.Grid(x, None, widths, splits=splits)
+    coords, counts, _ = g.cells()
+    assert counts.sum() == 400
+    for j in range(3):
+        assert sorted(set(coords[:, j].tolist())) == list(range(int(splits[j])))
+
+
+def _exhaustive(x, q, k):
+    rows = [refs.knn_exhaustive(x, qi, k) for qi in q]
+    return np.stack([r[0] for r in rows]), np.stack([r[1] for r in rows])
+
+
+def _exact_cases():
+    out = []
+    for seed, (n, d, w) in enumerate([(500, 2, 0.05), (800, 3, 0.11), (300, 4, 0.2),
+                                      (400, 1, 0.01), (250, 6, 0.4)]):
+        x, _, q = wl.uniform(n, 40, d, seed=600 + seed)
+        q = np.concatenate([q, np.full((2, d), -0.3), np.full((1, d), 1.7)]).astype(np.float32)
+        out.append((x, q, w, None))
+    # clustered points, per-dimension widths
+    rng = np.random.default_rng(5)
+    x = np.concatenate([rng.normal(0.3, 0.02, (300, 3)), rng.random((100, 3))]).astype(np.float32)
+    out.append((x, rng.random((40, 3)).astype(np.float32), np.float32([0.05, 0.02, 0.1]), None))
+    # lattice with exact ties
+    xl, _, ql = wl.lattice(12, 2, 40, seed=3)
+    out.append((xl, ql, 1.0, None))
+    return out
+
+
+@pytest.mark.parametrize("k", [1, 5, 16])
+def test_exact_rule_equals_exhaustive_knn(k):
+    for x, q, w, splits in _exact_cases():
+        g = oracle.Grid(x, None, w, splits=splits)
+        ids, d2, _ = g.query(q, k, -1, rule=oracle.RULE_EXACT)
+        e_ids, e_d2 = _exhaustive(x, q, k)
+        assert np.array_equal(ids, e_ids)
+        assert np.array_equal(d2.view(np.uint32), e_d2.view(np.uint32))
+
+
+def test_exact_rule_on_a_measured_grid_equals_exhaustive_knn():
+    rng = np.random.default_rng(8)
+    x = np.round(rng.random((600, 2)) * 50).astype(np.float32) / np.float32(50)
+    splits, widths = oracle.measure_cells(x)
+    g = oracle.Grid(x, None, widths, splits=splits)
+    q = rng.random((60, 2)).astype(np.float32) * np.float32(1.4) - np.float32(0.2)
+    ids, d2, _ = g.query(q, 7, -1, rule=oracle.RULE_EXACT)
+    e_ids, e_d2 = _exhaustive(x, q, 7)
+    assert np.array_equal(ids, e_ids)
+    assert np.array_equal(d2.view(np.uint32), e_d2.view(np.uint32))
+
+
+def test_exact_rule_stops_once_certified():
+    """On a unit lattice with w = 1 and k = 1, a query at a lattice point has
+    its neighbour at distance 0 in the central cell; the gap to the cells
+    beyond cube(1) is at least 1, so the walk stops after layer 1 (2 layers),
+    long before covering the 40 x 40 box."""
+    xl = np.stack(np.meshgrid(np.arange(40), np.arange(40)), -1).reshape(-1, 2).astype(np.float32)
+    g = oracle.Grid(xl, None, 1.0)
+    q = np.array([[20.0, 20.0], [7.0, 31.0]], np.float32)
+    _, _, _, st = g.query(q, 1, -1, stats=True, rule=oracle.RULE_EXACT)
+    assert st[:, 0].tolist() == [2, 2]
+    _, _, _, st0 = g.query(q, 1, -1, stats=True, rule=oracle.RULE_NONE)
+    assert (st0[:, 0] > 10).all()
+    # by the upper edge of the box no cell lies above, so only the other sides
+    # bound the unseen points: nearest (39, 20) at 0.95^2 + 0.5^2 = 1.1525,
+    # below the gap 1.5^2 left after layer 1 (dimension 1, both sides)
+    _, _, _, st = g.query(np.array([[39.95, 20.5]], np.float32), 1, -1, stats=True,
+                          rule=oracle.RULE_EXACT)
+    assert st[0, 0] == 2
