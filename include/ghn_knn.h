@@ -22,11 +22,13 @@
  *   - One device per index: the device current at knn_build time.
  *
  * Readings of points the paper leaves open, fixed by this library:
- *   - origin: per-dimension minimum of the training points; one cell width
- *     for all dimensions, given by the caller.
- *   - cell id (Eq. 1): c_j = floor((p_j - o_j) / w) in IEEE single precision,
- *     round to nearest; cells are half-open; query cells are clamped to
- *     [-2^40, 2^40].
+ *   - origin: per-dimension minimum of the training points; a cell width per
+ *     dimension (knn_build_grid) or one for all (knn_build), given by the
+ *     caller or measured by the paper's rule (knn_measure_cells).
+ *   - cell id (Eq. 1): c_j = floor((p_j - o_j) / w_j) in IEEE single
+ *     precision, round to nearest; cells are half-open; on a grid with split
+ *     counts, training cells are clamped to s_j - 1 (the last split is
+ *     closed); query cells are clamped to [-2^40, 2^40].
  *   - layer L: the cells at Chebyshev distance L from the central cell.
  *   - stop: after layer L when the k-buffer is full and no point of layer L
  *     entered it, or when the layers so far cover every occupied cell.
@@ -72,6 +74,11 @@ typedef int32_t knn_status;
 /* knn_query flags. */
 #define KNN_QUERY_CHECKED 1 /* synchronize `stream` and return the kernel's status */
 #define KNN_QUERY_SORTED 2  /* visit queries in cell order (locality in L2) */
+#define KNN_QUERY_EXACT 4   /* certified stop instead of the paper's rule: stop after
+                               layer L once the k-th squared distance is below the
+                               squared distance from the query to every cell outside
+                               cube(L), less rounding margins; the neighbours then
+                               equal exhaustive KNN's */
 
 typedef struct ghn_index ghn_index; /* opaque; owns all of its device memory */
 
@@ -109,6 +116,39 @@ knn_status knn_build(const float* points, const void* labels, int64_t n, int32_t
                      float cell_width, int32_t table, void* stream, ghn_index** out);
 
 /*
+ * knn_build_grid: knn_build with one cell measurement per dimension (Sec.
+ * III.A: cells are identical but not necessarily equilateral).
+ *   cell_widths  host, d positive finite widths.
+ *   splits       host, d split counts in [1, 2^31), or NULL: training cells
+ *                are clamped to splits[j] - 1, so that the largest value lies
+ *                in the last split (the grid of knn_measure_cells).
+ * Other arguments, errors and synchronisation as knn_build (which is
+ * knn_build_grid with every width equal and no splits).
+ */
+knn_status knn_build_grid(const float* points, const void* labels, int64_t n, int32_t d,
+                          const float* cell_widths, const int64_t* splits, int32_t table,
+                          void* stream, ghn_index** out);
+
+/*
+ * knn_measure_cells: the paper's cell measurement (Sec. III.A).  For each
+ * dimension, the largest number s of equal splits of the range of values
+ * [min, max] such that every split holds a training point, and the split
+ * width w = (max - min) / s in single precision.  A point's split is its
+ * Eq. 1 coordinate with width w, the last split closed (coordinates clamped
+ * to s - 1).  s is at most 2^21 (finer splits than single precision resolves
+ * over a range); a dimension with one value gets s = 1, w = 1.
+ *   points   host or device, n*d float32.
+ *   splits   host, d int64; cell_widths host, d float32 (receive the result).
+ * Synchronizes `stream`.  KNN_EINVAL for bad arguments or a non-finite value.
+ */
+knn_status knn_measure_cells(const float* points, int64_t n, int32_t d, int64_t* splits,
+                             float* cell_widths, void* stream);
+
+/* The widths and split counts an index was built with (host, d entries each;
+ * splits are 0 for a grid without them).  Either pointer may be NULL. */
+knn_status knn_index_grid(const ghn_index* index, float* cell_widths, int64_t* splits);
+
+/*
  * knn_query: exploration and prediction (Sec. III.B, Algorithm 2; Sec. I).
  *   index    from knn_build.
  *   queries  host or device, m*d float32, row-major.
@@ -120,7 +160,7 @@ knn_status knn_build(const float* points, const void* labels, int64_t n, int32_t
  *   dist2    host or device, m*k float32 squared distances (may be NULL).
  *   pred     host or device, m int32 (VOTE) or float32 (MEAN, MEDIAN), or
  *            NULL; NaN for MEAN / MEDIAN when no neighbour was found.
- *   flags    KNN_QUERY_CHECKED | KNN_QUERY_SORTED.
+ *   flags    KNN_QUERY_CHECKED | KNN_QUERY_SORTED | KNN_QUERY_EXACT.
  *   stream   cudaStream_t or NULL.
  * Device outputs are written asynchronously on `stream`; host outputs are
  * filled before the call returns.  A query with a non-finite coordinate gets
@@ -153,7 +193,8 @@ knn_status knn_query_stats(const ghn_index* index, const float* queries, int64_t
  *   Same arguments and results as knn_query, except:
  *   - queries, ids, dist2 and pred must be device memory (KNN_EINVAL if not);
  *   - 0 <= m <= 1048576 (KNN_EINVAL beyond);
- *   - flags: only KNN_QUERY_CHECKED (the locality order needs sort buffers).
+ *   - flags: KNN_QUERY_CHECKED and KNN_QUERY_EXACT only (the locality order
+ *     needs sort buffers).
  * The kernels' scratch lives in a fixed device array of the library (about
  * 4 MiB, held by every GPU that loads the library until exit).  The first call
  * on a device looks up that array's address, with the index's device current;
@@ -196,7 +237,7 @@ knn_status knn_batch_info(const ghn_batch* batch, int32_t i, knn_index_info_t* i
 /*
  * knn_batch_query: query every index of the batch (host arrays of count
  * entries; every data pointer is device memory; m[i] may be 0).  Outputs of
- * index i as knn_query's.  flags: KNN_QUERY_CHECKED only.
+ * index i as knn_query's.  flags: KNN_QUERY_CHECKED, KNN_QUERY_EXACT.
  */
 knn_status knn_batch_query(const ghn_batch* batch, const float* const* queries, const int64_t* m,
                            const int32_t* k, const int32_t* mode, int32_t* const* ids,

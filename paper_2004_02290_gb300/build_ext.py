@@ -19,7 +19,8 @@ LIB = os.path.join(OUT_DIR, "libghn_knn.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["capi.cu", "build_kernels.cu", "query_d12.cu", "query_d34.cu", "query_d56.cu",
-           "query_d78.cu", "noalloc.cu", "batch.cu", "serve.cu"]
+           "query_d78.cu", "noalloc.cu", "batch.cu", "serve.cu",
+           "measure.cu"]
 HEADERS = ["ghn_internal.cuh", "query_kernel.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

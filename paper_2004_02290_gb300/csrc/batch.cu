@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int j = 0; j < kMaxD; ++j) {
             if (j < d) {
-                const float t = __fdiv_rn(__fsub_rn(__ldg(p + j), ds.g.lo[j]), ds.g.w);
+                const float t = __fdiv_rn(__fsub_rn(__ldg(p + j), ds.g.lo[j]), ds.g.w[j]);
                 key += (unsigned long long)(long long)floorf(t) * ds.g.stride[j];
             }
         }
@@ -542,8 +542,10 @@ knn_status batch_build_impl(int count, const float* const* points, const void* c
             }
             GridConst& g = ds.g;
             memset(&g, 0, sizeof(g));
-            g.w = width[i];
-            g.inv_w = 1.0f / width[i];
+            for (int j = 0; j < kMaxD; ++j) {
+                g.w[j] = width[i];
+                g.inv_w[j] = 1.0f / width[i];
+            }
             g.d = d[i];
             unsigned long long space = 1ull;
             bool overflow = false;
@@ -927,14 +929,16 @@ knn_status knn_batch_query(const ghn_batch* batch, const float* const* queries, 
 {
     if (!batch || !queries || !m || !k || !mode || !ids)
         return fail("knn_batch_query: NULL argument", KNN_EINVAL);
-    if (flags & ~KNN_QUERY_CHECKED)
-        return fail("knn_batch_query: only KNN_QUERY_CHECKED is supported", KNN_EINVAL);
+    if (flags & ~(KNN_QUERY_CHECKED | KNN_QUERY_EXACT))
+        return fail("knn_batch_query: only KNN_QUERY_CHECKED and KNN_QUERY_EXACT are supported",
+                    KNN_EINVAL);
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != batch->device) cudaSetDevice(batch->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Layout lay;
     knn_status st = plan_layout(batch, queries, m, k, mode, ids, dist2, pred, lay);
+    for (QueryArgs& a : lay.args) a.exact = (flags & KNN_QUERY_EXACT) ? 1 : 0;
     ghn_plan p;
     p.device = batch->device;
     if (st == KNN_OK && !lay.args.empty()) {

@@ -73,12 +73,13 @@ __global__ void box_partial_kernel(const float* __restrict__ pts, long long tota
 
 // Reduce the partial boxes (one block: each thread folds a slice of the
 // partials, then a tree over the block); compute the number of cells per
-// dimension from the largest point: ext_j = floor((hi_j - lo_j) / w) + 1 (Eq. 1
-// is monotone in the coordinate, so no training point has a larger cell).
+// dimension from the largest point: ext_j = floor((hi_j - lo_j) / w_j) + 1 (Eq. 1
+// is monotone in the coordinate, so no training point has a larger cell),
+// at most split_j when the grid clamps training cells into split_j splits.
 constexpr int kBoxFinalThreads = 256;
 
 __global__ void __launch_bounds__(kBoxFinalThreads)
-    box_final_kernel(const float* __restrict__ partial, int nblocks, int d, float w,
+    box_final_kernel(const float* __restrict__ partial, int nblocks, int d, const Widths w,
                      BoxOut* __restrict__ out)
 {
     __shared__ float slo[kMaxD][kBoxFinalThreads];
@@ -131,11 +132,12 @@ __global__ void __launch_bounds__(kBoxFinalThreads)
             if (sbad || !(l <= h)) {
                 flags |= kStatusNonFinite;
             } else {
-                const float q = __fdiv_rn(__fsub_rn(h, l), w);
+                const float q = __fdiv_rn(__fsub_rn(h, l), w.w[j]);
                 if (!(q < 2147483647.0f))
                     flags |= kStatusExtent;
                 else
                     ext = (long long)floorf(q) + 1;
+                if (w.split[j] > 0 && ext > w.split[j]) ext = w.split[j];
             }
             out->ext[j] = ext;
         }
@@ -144,9 +146,10 @@ __global__ void __launch_bounds__(kBoxFinalThreads)
 }
 
 // ---------------------------------------------------------------------------
-// Eq. 1 for every training point: c_j = floor((p_j - o_j) / w) in single
-// precision (subtract and divide rounded to nearest, as IEEE operations), then
-// the linear id sum_j c_j * stride_j; the value is the point's index.
+// Eq. 1 for every training point: c_j = floor((p_j - o_j) / w_j) in single
+// precision (subtract and divide rounded to nearest, as IEEE operations),
+// clamped to split_j - 1 on a grid with splits, then the linear id
+// sum_j c_j * stride_j; the value is the point's index.
 // ---------------------------------------------------------------------------
 template <int D>
 __global__ void cell_keys_kernel(const float* __restrict__ pts, long long n, GridConst g,
@@ -158,8 +161,9 @@ __global__ void cell_keys_kernel(const float* __restrict__ pts, long long n, Gri
         unsigned long long key = 0;
 #pragma unroll
         for (int j = 0; j < D; ++j) {
-            const float t = __fdiv_rn(__fsub_rn(__ldg(pts + i * D + j), g.lo[j]), g.w);
-            const long long c = (long long)floorf(t);
+            const float t = __fdiv_rn(__fsub_rn(__ldg(pts + i * D + j), g.lo[j]), g.w[j]);
+            long long c = (long long)floorf(t);
+            if (g.split[j] > 0 && c > g.split[j] - 1) c = g.split[j] - 1;
             key += (unsigned long long)c * g.stride[j];
         }
         keys[i] = key;
@@ -508,7 +512,7 @@ __global__ void query_keys_kernel(const float* __restrict__ q, long long m, Grid
         unsigned long long key = 0;
 #pragma unroll
         for (int j = 0; j < D; ++j) {
-            float t = floorf(__fdiv_rn(__fsub_rn(__ldg(q + i * D + j), g.lo[j]), g.w));
+            float t = floorf(__fdiv_rn(__fsub_rn(__ldg(q + i * D + j), g.lo[j]), g.w[j]));
             t = fminf(fmaxf(t, 0.0f), (float)g.cmax[j]);  // NaN becomes 0
             long long c = (long long)t;
             if (c > g.cmax[j]) c = g.cmax[j];
@@ -541,7 +545,7 @@ int box_partial_blocks(long long n)
     return (int)b;
 }
 
-cudaError_t launch_box(const float* pts, long long n, int d, float w, float* partial,
+cudaError_t launch_box(const float* pts, long long n, int d, const Widths& w, float* partial,
                        int partial_blocks, BoxOut* out, cudaStream_t s)
 {
     const int threads = 64 * d;

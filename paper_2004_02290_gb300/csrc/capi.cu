@@ -21,7 +21,7 @@ struct ghn_index {
     int device = 0;
     long long n = 0;
     int d = 0;
-    float w = 0.0f;
+    Widths wd{};  // cell measurement and split count of each dimension
     int table = KNN_TABLE_DENSE;
     GridConst g{};
     unsigned long long ncell_space = 0;  // cells in the box (prod of extents)
@@ -287,7 +287,7 @@ void free_index(ghn_index* x)
 }
 
 knn_status build_impl(const float* points_user, const void* labels_user, long long n, int d,
-                      float w, int table, cudaStream_t s, ghn_index** out)
+                      const Widths& wd, int table, cudaStream_t s, ghn_index** out)
 {
     int dev = 0;
     GHN_CHECK(cudaGetDevice(&dev), "cudaGetDevice");
@@ -303,7 +303,7 @@ knn_status build_impl(const float* points_user, const void* labels_user, long lo
     x->device = dev;
     x->n = n;
     x->d = d;
-    x->w = w;
+    x->wd = wd;
     knn_status st = KNN_OK;
     g_timer.begin(s);
     {
@@ -330,7 +330,7 @@ knn_status build_impl(const float* points_user, const void* labels_user, long lo
             return fail(st);
         }
         BoxOut box;
-        cudaError_t e = launch_box(pts, n, d, w, partial, pb, box_dev, s);
+        cudaError_t e = launch_box(pts, n, d, wd, partial, pb, box_dev, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&box, box_dev, sizeof(box), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) {
@@ -347,8 +347,11 @@ knn_status build_impl(const float* points_user, const void* labels_user, long lo
         }
         GridConst& g = x->g;
         memset(&g, 0, sizeof(g));
-        g.w = w;
-        g.inv_w = 1.0f / w;
+        for (int j = 0; j < d; ++j) {
+            g.w[j] = wd.w[j];
+            g.inv_w[j] = 1.0f / wd.w[j];
+            g.split[j] = wd.split[j];
+        }
         g.d = d;
         unsigned long long space = 1ull;
         bool overflow = false;
@@ -570,6 +573,7 @@ knn_status query_impl(const ghn_index* x, const float* queries_user, long long m
         a.order = order;
         a.max_layers = max_layers_env();
         a.dense = x->table == KNN_TABLE_DENSE;
+        a.exact = (flags & KNN_QUERY_EXACT) ? 1 : 0;
         GHN_CHECK(launch_query(a, num_sms(x->device), s), "query kernel");
         g_timer.mark("search", s);
 
@@ -724,6 +728,15 @@ extern "C" {
 knn_status knn_build(const float* points, const void* labels, int64_t n, int32_t d,
                      float cell_width, int32_t table, void* stream, ghn_index** out)
 {
+    float widths[kMaxD];
+    for (int j = 0; j < kMaxD; ++j) widths[j] = cell_width;
+    return knn_build_grid(points, labels, n, d, widths, nullptr, table, stream, out);
+}
+
+knn_status knn_build_grid(const float* points, const void* labels, int64_t n, int32_t d,
+                          const float* cell_widths, const int64_t* splits, int32_t table,
+                          void* stream, ghn_index** out)
+{
     if (!out) {
         set_err("knn_build: out is NULL");
         return KNN_EINVAL;
@@ -741,16 +754,41 @@ knn_status knn_build(const float* points, const void* labels, int64_t n, int32_t
         set_err("knn_build: d = %d outside [1, %d]", d, kMaxD);
         return KNN_EINVAL;
     }
-    if (!(cell_width > 0.0f) || !isfinite(cell_width)) {
-        set_err("knn_build: cell width must be a positive finite number");
+    if (!cell_widths) {
+        set_err("knn_build: cell widths are NULL");
         return KNN_EINVAL;
+    }
+    Widths wd{};
+    for (int j = 0; j < d; ++j) {
+        if (!(cell_widths[j] > 0.0f) || !isfinite(cell_widths[j])) {
+            set_err("knn_build: cell width must be a positive finite number");
+            return KNN_EINVAL;
+        }
+        if (splits && (splits[j] < 1 || splits[j] >= (1ll << 31))) {
+            set_err("knn_build: split counts must be in [1, 2^31)");
+            return KNN_EINVAL;
+        }
+        wd.w[j] = cell_widths[j];
+        wd.split[j] = splits ? splits[j] : 0;
     }
     if (table < KNN_TABLE_AUTO || table > KNN_TABLE_HASH) {
         set_err("knn_build: unknown table kind %d", table);
         return KNN_EINVAL;
     }
-    return build_impl(points, labels, n, d, cell_width, table, static_cast<cudaStream_t>(stream),
-                      out);
+    return build_impl(points, labels, n, d, wd, table, static_cast<cudaStream_t>(stream), out);
+}
+
+knn_status knn_index_grid(const ghn_index* index, float* cell_widths, int64_t* splits)
+{
+    if (!index) {
+        set_err("knn_index_grid: index is NULL");
+        return KNN_EINVAL;
+    }
+    for (int j = 0; j < index->d; ++j) {
+        if (cell_widths) cell_widths[j] = index->wd.w[j];
+        if (splits) splits[j] = index->wd.split[j];
+    }
+    return KNN_OK;
 }
 
 knn_status knn_query(const ghn_index* index, const float* queries, int64_t m, int32_t k,
@@ -796,7 +834,7 @@ knn_status knn_index_info(const ghn_index* index, knn_index_info_t* info)
     info->n = x->n;
     info->d = x->d;
     info->table = x->table;
-    info->cell_width = x->w;
+    info->cell_width = x->wd.w[0];
     for (int j = 0; j < x->d; ++j) {
         info->origin[j] = x->g.lo[j];
         info->extent[j] = x->g.cmax[j] + 1;

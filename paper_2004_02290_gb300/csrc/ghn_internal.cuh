@@ -19,11 +19,18 @@ constexpr unsigned int kStatusExtent = 4u;     // too many cells along one dimen
 // Grid geometry, passed by value to the kernels.
 struct GridConst {
     float lo[kMaxD];                 // origin: per-dimension minimum
-    float w;                         // cell width
-    float inv_w;                     // 1 / w rounded (bounds only, never Eq. 1)
+    float w[kMaxD];                  // cell measurement of each dimension
+    float inv_w[kMaxD];              // 1 / w_j rounded (bounds only, never Eq. 1)
     int d;
     long long cmax[kMaxD];           // largest occupied cell coordinate (extent - 1)
     unsigned long long stride[kMaxD];  // linear id = sum c_j * stride_j, stride_{d-1} = 1
+    long long split[kMaxD];          // training cells clamped to split_j - 1 (0: no clamp)
+};
+
+// Cell measurements of a build: a width and an optional split count per dimension.
+struct Widths {
+    float w[kMaxD];
+    long long split[kMaxD];  // 0: no clamp
 };
 
 // Results of the build that only the device knows without a sync.
@@ -64,7 +71,7 @@ __host__ __device__ constexpr int row_floats(int d) { return d <= 2 ? 2 : (d <= 
 void count_launches(long long k);
 
 // ---- build launchers (build_kernels.cu) ----
-cudaError_t launch_box(const float* pts, long long n, int d, float w, float* partial,
+cudaError_t launch_box(const float* pts, long long n, int d, const Widths& w, float* partial,
                        int partial_blocks, BoxOut* out, cudaStream_t s);
 int box_partial_blocks(long long n);
 
@@ -140,6 +147,7 @@ struct QueryArgs {
     const unsigned int* order;      // visiting order of queries or null
     long long max_layers;           // 0 = no cap
     int dense;
+    int exact;                      // certified stop instead of the paper's rule
 };
 
 cudaError_t launch_query(const QueryArgs& a, int num_sms, cudaStream_t s);

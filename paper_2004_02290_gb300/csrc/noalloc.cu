@@ -91,9 +91,9 @@ extern "C" knn_status knn_query_noalloc(const ghn_index* index, const float* que
         ghn::set_error("knn_query_noalloc: a prediction needs labels, and the index has none");
         return KNN_EINVAL;
     }
-    if (flags & ~KNN_QUERY_CHECKED) {
-        ghn::set_error("knn_query_noalloc: only KNN_QUERY_CHECKED is supported (the locality "
-                       "order needs sort buffers)");
+    if (flags & ~(KNN_QUERY_CHECKED | KNN_QUERY_EXACT)) {
+        ghn::set_error("knn_query_noalloc: only KNN_QUERY_CHECKED and KNN_QUERY_EXACT are "
+                       "supported (the locality order needs sort buffers)");
         return KNN_EINVAL;
     }
     if (m == 0) return KNN_OK;
@@ -131,6 +131,7 @@ extern "C" knn_status knn_query_noalloc(const ghn_index* index, const float* que
             a.ids = ids;
             a.dist2 = dist2;
             a.pred = mode >= 0 ? pred : nullptr;
+            a.exact = (flags & KNN_QUERY_EXACT) ? 1 : 0;
             a.counter = reinterpret_cast<unsigned long long*>(scratch);
             a.status = reinterpret_cast<unsigned int*>(scratch + 8);
             a.heavy_count = reinterpret_cast<unsigned int*>(scratch + 16);

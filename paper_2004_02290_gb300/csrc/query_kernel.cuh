@@ -342,7 +342,7 @@ __device__ __forceinline__ void query_setup(const QueryArgs& a, long long qid, Q
 #pragma unroll
     for (int j = 0; j < D; ++j) {
         // Eq. 1 on the query, single precision, round to nearest
-        s.u[j] = __fdiv_rn(__fsub_rn(s.q[j], a.g.lo[j]), a.g.w);
+        s.u[j] = __fdiv_rn(__fsub_rn(s.q[j], a.g.lo[j]), a.g.w[j]);
         float f = floorf(s.u[j]);
         f = fminf(fmaxf(f, -kQueryClamp), kQueryClamp);  // NaN becomes -2^40
         s.c0[j] = (long long)f;
@@ -376,12 +376,13 @@ __device__ __forceinline__ void layer_box(const QueryArgs& a, const Query<D>& s,
     }
     if (!skipping) return;
     // a cell farther than kd along one axis cannot hold a point that enters;
-    // the radius r = sqrt(kd) / w in cell units is taken with fast approximate
-    // operations (errors near 1e-6) and widened by 1e-4
-    const float r = (kd > 0.0f ? kd * rsqrtf(kd) : 0.0f) * a.g.inv_w * (1.0f + 1e-4f);
+    // the radius r_j = sqrt(kd) / w_j in cell units is taken with fast
+    // approximate operations (errors near 1e-6) and widened by 1e-4
+    const float rk = (kd > 0.0f ? kd * rsqrtf(kd) : 0.0f) * (1.0f + 1e-4f);
     bool shell = false;
 #pragma unroll
     for (int j = 0; j < D; ++j) {
+        const float r = rk * a.g.inv_w[j];
         const float m = 1e-5f * (fabsf(s.u[j]) + r) + 1e-3f;
         const float a0f = floorf(s.u[j] - r - m), a1f = floorf(s.u[j] + r + m);
         // beyond the int range the clip would not tighten the box anyway
@@ -396,6 +397,38 @@ __device__ __forceinline__ void layer_box(const QueryArgs& a, const Query<D>& s,
                  (s.c0[j] + L >= b.lo[j] && s.c0[j] + L <= b.hi[j]);
     }
     b.empty |= !shell;
+}
+
+// The certified stop (a variant of the paper's rule whose result equals
+// exhaustive KNN): after cube(L), a training point in a cell beyond
+// c0_j + L along axis j lies at or above o_j + (c0_j + L + 1) w_j, and one
+// below c0_j - L lies under o_j + (c0_j - L) w_j, each up to the rounding of
+// Eq. 1 (taken as a relative 2^-21 of the edge's quotient).  Sides where the
+// box holds no cell beyond cube(L) do not count.  The smallest gap bounds
+// every unseen point's distance, whose single-precision square is at least
+// gap^2 (1 - 2^-20); the walk may stop when the k-th squared distance is
+// below that.  Double precision, evaluated once per layer.
+template <int D>
+__device__ __forceinline__ bool certified(const QueryArgs& a, const Query<D>& s, long long L,
+                                          float kth_d)
+{
+    double gap = INFINITY;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const double w = (double)a.g.w[j], o = (double)a.g.lo[j], qj = (double)s.q[j];
+        if (s.c0[j] + L < a.g.cmax[j]) {
+            const double cu = (double)(s.c0[j] + L + 1);
+            const double edge = o + cu * w - fabs(cu) * w * 0x1p-21;
+            gap = fmin(gap, edge - qj);
+        }
+        if (s.c0[j] - L > 0) {
+            const double cl = (double)(s.c0[j] - L);
+            const double edge = o + cl * w + fabs(cl) * w * 0x1p-21;
+            gap = fmin(gap, qj - edge);
+        }
+    }
+    if (!(gap > 0.0)) return false;
+    return (double)kth_d < gap * gap * (1.0 - 0x1p-20);
 }
 
 template <int D>
@@ -459,7 +492,7 @@ __device__ __forceinline__ void row_ranges(const QueryArgs& a, unsigned long lon
         const long long dd = c > s.c0[j] ? c - s.c0[j] : s.c0[j] - c;
         ocheb = dd > ocheb ? dd : ocheb;
         base += (unsigned long long)c * a.g.stride[j];
-        og2 += axis_gap2(c, c, s.u[j], a.g.w);
+        og2 += axis_gap2(c, c, s.u[j], a.g.w[j]);
     }
     long long x0a, x1a, x0b, x1b;
     if (ocheb == L) {
@@ -487,7 +520,7 @@ __device__ __forceinline__ void row_ranges(const QueryArgs& a, unsigned long lon
         // An infinite k-th distance (overflowed squares) clips nothing.
         const float rem = kth_d * (1.0f + 2e-5f) - og2;
         if (rem < 0.0f) return;
-        const float r = (rem > 0.0f ? rem * rsqrtf(rem) : 0.0f) * a.g.inv_w * (1.0f + 1e-4f);
+        const float r = (rem > 0.0f ? rem * rsqrtf(rem) : 0.0f) * a.g.inv_w[dl] * (1.0f + 1e-4f);
         const float u = s.u[dl];
         const float m = 1e-5f * (fabsf(u) + r) + 1e-3f;
         const float c0f = floorf(u - r - m), c1f = floorf(u + r + m);
@@ -500,10 +533,10 @@ __device__ __forceinline__ void row_ranges(const QueryArgs& a, unsigned long lon
         x1b = x1b < c1 ? x1b : c1;
     }
     if (x0a <= x1a &&
-        !(prune && (og2 + axis_gap2(x0a, x1a, s.u[dl], a.g.w)) * (1.0f - 1e-5f) > kth_d))
+        !(prune && (og2 + axis_gap2(x0a, x1a, s.u[dl], a.g.w[dl])) * (1.0f - 1e-5f) > kth_d))
         resolve_run<DENSE>(a, hmask, base, x0a, x1a, counting, sa, la, cells);
     if (x0b <= x1b &&
-        !(prune && (og2 + axis_gap2(x0b, x1b, s.u[dl], a.g.w)) * (1.0f - 1e-5f) > kth_d))
+        !(prune && (og2 + axis_gap2(x0b, x1b, s.u[dl], a.g.w[dl])) * (1.0f - 1e-5f) > kth_d))
         resolve_run<DENSE>(a, hmask, base, x0b, x1b, counting, sb, lb, cells);
     if (la == 0u) {
         sa = sb;
@@ -831,7 +864,9 @@ __device__ __forceinline__ bool walk_query(const QueryArgs& a, long long qid, Wa
             }
             if (deferred) break;
         }
-        if (tk.count == tk.k && !updated) break;  // the stop rule of Sec. III.B
+        if (tk.count == tk.k &&
+            (a.exact ? certified(a, s, L, __uint_as_float((unsigned)(tk.kth >> 32))) : !updated))
+            break;  // the stop rule of Sec. III.B (or the certified one)
         if (b.covers) break;                      // every occupied cell seen
         if (a.max_layers > 0 && L - s.lmin + 1 >= a.max_layers) {
             limited = true;
@@ -1063,7 +1098,9 @@ __device__ __forceinline__ void coop_query(const QueryArgs& a, long long qid, Co
         __syncthreads();
         const bool updated = sm.updated != 0;
         const bool full = sm.count == a.k;
-        if (full && !updated) break;  // the stop rule of Sec. III.B
+        if (full && (a.exact ? certified(a, s, L, __uint_as_float((unsigned)(sm.top[a.k - 1] >> 32)))
+                             : !updated))
+            break;  // the stop rule of Sec. III.B (or the certified one)
         if (b.covers) break;
         if (a.max_layers > 0 && L - s.lmin + 1 >= a.max_layers) {
             limited = true;

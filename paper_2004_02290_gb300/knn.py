@@ -16,7 +16,7 @@ import numpy as np
 KNN_OK, KNN_EINVAL, KNN_ENOMEM, KNN_ECUDA, KNN_ELIMIT, KNN_ETIMEDOUT = 0, 1, 2, 3, 4, 5
 KNN_NONE, KNN_VOTE, KNN_MEAN, KNN_MEDIAN = -1, 0, 1, 2
 KNN_TABLE_AUTO, KNN_TABLE_DENSE, KNN_TABLE_HASH = 0, 1, 2
-KNN_QUERY_CHECKED, KNN_QUERY_SORTED = 1, 2
+KNN_QUERY_CHECKED, KNN_QUERY_SORTED, KNN_QUERY_EXACT = 1, 2, 4
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libghn_knn.so")
@@ -41,7 +41,7 @@ class knn_index_info_t(ctypes.Structure):
 
 EXPORTED = ["knn_batch_build", "knn_batch_info", "knn_batch_query", "knn_batch_plan",
             "knn_batch_run", "knn_plan_free", "knn_batch_free",
-            "knn_build", "knn_query", "knn_query_stats", "knn_query_noalloc", "knn_index_info",
+            "knn_build", "knn_build_grid", "knn_measure_cells", "knn_index_grid", "knn_query", "knn_query_stats", "knn_query_noalloc", "knn_index_info",
             "knn_index_export",
             "knn_timing_enable", "knn_timing_read", "knn_kernel_launches", "knn_free",
             "knn_last_error", "knn_abi_version",
@@ -86,6 +86,12 @@ def library(path: str | None = None) -> ctypes.CDLL:
         vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
         lib.knn_build.argtypes = [vp, vp, i64, i32, ctypes.c_float, i32, vp, ctypes.POINTER(vp)]
         lib.knn_build.restype = i32
+        lib.knn_build_grid.argtypes = [vp, vp, i64, i32, vp, vp, i32, vp, ctypes.POINTER(vp)]
+        lib.knn_build_grid.restype = i32
+        lib.knn_measure_cells.argtypes = [vp, i64, i32, vp, vp, vp]
+        lib.knn_measure_cells.restype = i32
+        lib.knn_index_grid.argtypes = [vp, vp, vp]
+        lib.knn_index_grid.restype = i32
         lib.knn_query.argtypes = [vp, vp, i64, i32, i32, vp, vp, vp, i32, vp]
         lib.knn_query.restype = i32
         lib.knn_query_stats.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp]
@@ -210,6 +216,13 @@ class Index:
         _check(library().knn_index_info(self._h, ctypes.byref(out)))
         return out
 
+    def grid(self):
+        """(widths float32[d], splits int64[d]) the index was built with (splits 0: none)."""
+        w = np.zeros(self.d, np.float32)
+        sp = np.zeros(self.d, np.int64)
+        _check(library().knn_index_grid(self._h, w.ctypes.data, sp.ctypes.data))
+        return w, sp
+
     def export(self):
         """(cell_keys uint64, cell_start uint32, rows int32) as numpy arrays."""
         inf = self.info()
@@ -257,6 +270,43 @@ def knn_build(points, labels=None, cell_width: float = 1.0, table: int = KNN_TAB
                                table, _stream(stream, points, labels), ctypes.byref(h)))
     del keep_p, keep_l
     return Index(h, n, d)
+
+
+def knn_build_grid(points, labels=None, cell_widths=None, splits=None,
+                   table: int = KNN_TABLE_AUTO, stream=None) -> Index:
+    """Cell sampling with one cell measurement per dimension (and optional split counts)."""
+    if points.ndim != 2:
+        raise ValueError("points must be n x d")
+    _check_f32(points, "points")
+    n, d = int(points.shape[0]), int(points.shape[1])
+    w = np.ascontiguousarray(np.broadcast_to(np.asarray(cell_widths, np.float32), (d,)),
+                             np.float32)
+    sp = None if splits is None else np.ascontiguousarray(splits, np.int64)
+    if sp is not None and sp.shape != (d,):
+        raise ValueError("splits must have d entries")
+    pp, keep_p = _ptr(points)
+    lp, keep_l = _ptr(labels)
+    h = ctypes.c_void_p()
+    _check(library().knn_build_grid(pp, lp, n, d, w.ctypes.data,
+                                    sp.ctypes.data if sp is not None else None, table,
+                                    _stream(stream, points, labels), ctypes.byref(h)))
+    del keep_p, keep_l
+    return Index(h, n, d)
+
+
+def knn_measure_cells(points, stream=None):
+    """The paper's cell measurement (Sec. III.A) on the GPU: (splits int64[d], widths float32[d])."""
+    if points.ndim != 2:
+        raise ValueError("points must be n x d")
+    _check_f32(points, "points")
+    n, d = int(points.shape[0]), int(points.shape[1])
+    splits = np.zeros(d, np.int64)
+    widths = np.zeros(d, np.float32)
+    pp, keep = _ptr(points)
+    _check(library().knn_measure_cells(pp, n, d, splits.ctypes.data, widths.ctypes.data,
+                                       _stream(stream, points)))
+    del keep
+    return splits, widths
 
 
 def _alloc_like(ref, shape, dtype_name):
