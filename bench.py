@@ -354,6 +354,7 @@ def run_ours(args):
     info = idx.info()
     _, _, st = knn.knn_query_stats(idx, q, w.k, stream=stream)
     stats = st.cpu().numpy()
+    recall = recall_vs_exact(knn, idx, q, w, ids, stream)
     idx.free()
     peaks, peak_kind = measured_peaks()
     q_ms = phase_ms["query.search"]
@@ -400,10 +401,38 @@ def run_ours(args):
                                        if k.startswith("query.")) * 1e-3),
         "layers_mean": float(stats[:, 0].mean()),
         "step_ms_median": float(np.median(step_ms)),
+        "recall_vs_exact": recall,
     }
     print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def recall_vs_exact(knn, idx, q, w, ids_paper, stream):
+    """Recall of the paper's stop rule against exact KNN (KNN_QUERY_EXACT,
+    whose neighbours equal exhaustive KNN's): the share of the exact k
+    neighbours that the paper's rule returned, and the exact query's time."""
+    import torch
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    with torch.cuda.stream(stream):
+        ev[0].record(stream)
+    ex_ids, _, _ = knn.knn_query(idx, q, w.k, knn.KNN_NONE, flags=knn.KNN_QUERY_EXACT,
+                                 stream=stream)
+    with torch.cuda.stream(stream):
+        ev[1].record(stream)
+    ev[1].synchronize()
+    a = ids_paper.cpu().numpy()
+    b = ex_ids.cpu().numpy()
+    hit = 0
+    for ra, rb in zip(a, b):
+        rb = rb[rb >= 0]
+        hit += np.intersect1d(ra, rb, assume_unique=True).size
+    total = int((b >= 0).sum())
+    return {"recall": hit / max(1, total),
+            "queries_with_all_k": float(np.mean([np.array_equal(np.sort(ra), np.sort(rb))
+                                                 for ra, rb in zip(a, b)])),
+            "exact_query_ms": ev[0].elapsed_time(ev[1])}
 
 
 def run_e2e(w, knn, dev, args):

@@ -843,6 +843,7 @@ knn_status make_plan(const ghn_batch* b, Layout& lay, cudaStream_t s, ghn_plan* 
         ba.heavy_count = reinterpret_cast<unsigned int*>(p->counters + 2 * g + 1);
         ba.heavy_cursor = ba.heavy_count + 1;
         ba.heavy_list = heavy + hoff;
+        ba.exact = lay.args[lay.group_first[g]].exact;  // one rule for the whole call
         hoff += lay.group_total[g];
         p->groups.push_back(ba);
     }

@@ -164,6 +164,7 @@ struct BatchArgs {
     unsigned int* heavy_list;        // total entries, or null: no deferral
     unsigned int* heavy_count;       // zero at launch
     unsigned int* heavy_cursor;      // zero at launch
+    int exact;                       // certified stop for every index of the group
 };
 
 cudaError_t launch_batch_query(const BatchArgs& g, int num_sms, cudaStream_t s);

@@ -400,35 +400,30 @@ __device__ __forceinline__ void layer_box(const QueryArgs& a, const Query<D>& s,
 }
 
 // The certified stop (a variant of the paper's rule whose result equals
-// exhaustive KNN): after cube(L), a training point in a cell beyond
-// c0_j + L along axis j lies at or above o_j + (c0_j + L + 1) w_j, and one
-// below c0_j - L lies under o_j + (c0_j - L) w_j, each up to the rounding of
-// Eq. 1 (taken as a relative 2^-21 of the edge's quotient).  Sides where the
-// box holds no cell beyond cube(L) do not count.  The smallest gap bounds
-// every unseen point's distance, whose single-precision square is at least
-// gap^2 (1 - 2^-20); the walk may stop when the k-th squared distance is
-// below that.  Double precision, evaluated once per layer.
+// exhaustive KNN): after cube(L), every training point not yet seen lies in a
+// cell beyond c0_j + L or below c0_j - L along some axis j where the box still
+// holds cells.  The nearest such cell on each side bounds its distance from
+// below (axis_gap2: the gap in cell units less the rounding margin of Eq. 1,
+// scaled by w_j); the walk may stop when the smallest of these bounds, less
+// the rounding of a single-precision squared distance, exceeds the k-th
+// squared distance, which is the skipping test applied to every unseen cell.
 template <int D>
 __device__ __forceinline__ bool certified(const QueryArgs& a, const Query<D>& s, long long L,
                                           float kth_d)
 {
-    double gap = INFINITY;
+    float g2 = INFINITY;
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-        const double w = (double)a.g.w[j], o = (double)a.g.lo[j], qj = (double)s.q[j];
         if (s.c0[j] + L < a.g.cmax[j]) {
-            const double cu = (double)(s.c0[j] + L + 1);
-            const double edge = o + cu * w - fabs(cu) * w * 0x1p-21;
-            gap = fmin(gap, edge - qj);
+            const long long c = s.c0[j] + L + 1;
+            g2 = fminf(g2, axis_gap2(c, c, s.u[j], a.g.w[j]));
         }
         if (s.c0[j] - L > 0) {
-            const double cl = (double)(s.c0[j] - L);
-            const double edge = o + cl * w + fabs(cl) * w * 0x1p-21;
-            gap = fmin(gap, qj - edge);
+            const long long c = s.c0[j] - L - 1;
+            g2 = fminf(g2, axis_gap2(c, c, s.u[j], a.g.w[j]));
         }
     }
-    if (!(gap > 0.0)) return false;
-    return (double)kth_d < gap * gap * (1.0 - 0x1p-20);
+    return g2 * (1.0f - 1e-5f) > kth_d;
 }
 
 template <int D>
@@ -764,7 +759,7 @@ struct WarpSmem {
 
 // One query by one warp.  Returns true when the query was deferred to the
 // cooperative kernel (nothing written); otherwise its outputs are written.
-template <int D, int NS, bool DENSE>
+template <int D, int NS, bool DENSE, bool EXACT>
 __device__ __forceinline__ bool walk_query(const QueryArgs& a, long long qid, WarpSmem& sm,
                                            int lane, bool counting, bool may_defer)
 {
@@ -864,9 +859,13 @@ __device__ __forceinline__ bool walk_query(const QueryArgs& a, long long qid, Wa
             }
             if (deferred) break;
         }
-        if (tk.count == tk.k &&
-            (a.exact ? certified(a, s, L, __uint_as_float((unsigned)(tk.kth >> 32))) : !updated))
-            break;  // the stop rule of Sec. III.B (or the certified one)
+        // the stop rule of Sec. III.B, or the certified one (compiled apart)
+        if constexpr (EXACT) {
+            if (tk.count == tk.k && certified(a, s, L, __uint_as_float((unsigned)(tk.kth >> 32))))
+                break;
+        } else {
+            if (tk.count == tk.k && !updated) break;
+        }
         if (b.covers) break;                      // every occupied cell seen
         if (a.max_layers > 0 && L - s.lmin + 1 >= a.max_layers) {
             limited = true;
@@ -892,7 +891,7 @@ __device__ __forceinline__ bool walk_query(const QueryArgs& a, long long qid, Wa
     return false;
 }
 
-template <int D, int NS, bool DENSE>
+template <int D, int NS, bool DENSE, bool EXACT>
 __global__ void __launch_bounds__(kThreads, (MinBlocks<D, NS>::value))
     query_kernel(const QueryArgs a)
 {
@@ -911,7 +910,8 @@ __global__ void __launch_bounds__(kThreads, (MinBlocks<D, NS>::value))
         const unsigned long long qi = next;
         if (lane == 0) next = atomicAdd(a.counter, 1ull);
         const long long qid = a.order ? (long long)a.order[qi] : (long long)qi;
-        if (walk_query<D, NS, DENSE>(a, qid, sm[wib], lane, counting, may_defer) && lane == 0) {
+        if (walk_query<D, NS, DENSE, EXACT>(a, qid, sm[wib], lane, counting, may_defer) &&
+            lane == 0) {
             // too much work for one warp: the cooperative kernel takes it
             a.heavy_list[atomicAdd(a.heavy_count, 1u)] = (unsigned int)qid;
         }
@@ -948,7 +948,7 @@ struct CoopSmem {
 };
 
 // One query by the whole block (every thread calls it).
-template <int D, int NS, bool DENSE>
+template <int D, int NS, bool DENSE, bool EXACT>
 __device__ __forceinline__ void coop_query(const QueryArgs& a, long long qid, CoopSmem& sm)
 {
     const int lane = threadIdx.x & 31;
@@ -1098,9 +1098,13 @@ __device__ __forceinline__ void coop_query(const QueryArgs& a, long long qid, Co
         __syncthreads();
         const bool updated = sm.updated != 0;
         const bool full = sm.count == a.k;
-        if (full && (a.exact ? certified(a, s, L, __uint_as_float((unsigned)(sm.top[a.k - 1] >> 32)))
-                             : !updated))
-            break;  // the stop rule of Sec. III.B (or the certified one)
+        // the stop rule of Sec. III.B, or the certified one (compiled apart)
+        if constexpr (EXACT) {
+            if (full && certified(a, s, L, __uint_as_float((unsigned)(sm.top[a.k - 1] >> 32))))
+                break;
+        } else {
+            if (full && !updated) break;
+        }
         if (b.covers) break;
         if (a.max_layers > 0 && L - s.lmin + 1 >= a.max_layers) {
             limited = true;
@@ -1120,7 +1124,7 @@ __device__ __forceinline__ void coop_query(const QueryArgs& a, long long qid, Co
     __syncthreads();
 }
 
-template <int D, int NS, bool DENSE>
+template <int D, int NS, bool DENSE, bool EXACT>
 __global__ void __launch_bounds__(kThreads, 1) heavy_kernel(const QueryArgs a)
 {
     __shared__ CoopSmem sm;
@@ -1132,7 +1136,7 @@ __global__ void __launch_bounds__(kThreads, 1) heavy_kernel(const QueryArgs a)
         const unsigned int h = s_h;
         __syncthreads();
         if (h >= nheavy) break;
-        coop_query<D, NS, DENSE>(a, (long long)a.heavy_list[h], sm);
+        coop_query<D, NS, DENSE, EXACT>(a, (long long)a.heavy_list[h], sm);
     }
 }
 
@@ -1157,7 +1161,7 @@ __device__ __forceinline__ int group_index(const unsigned long long* qoff, int c
     return lo;
 }
 
-template <int D>
+template <int D, bool EXACT>
 __global__ void __launch_bounds__(kThreads, (MinBlocks<D, 1>::value))
     batch_query_kernel(const BatchArgs g)
 {
@@ -1176,17 +1180,19 @@ __global__ void __launch_bounds__(kThreads, (MinBlocks<D, 1>::value))
         const long long qid = (long long)(qi - __ldg(g.qoff + i));
         bool deferred;
         if (a.k <= 32)
-            deferred = a.dense ? walk_query<D, 1, true>(a, qid, sm[wib], lane, false, may_defer)
-                               : walk_query<D, 1, false>(a, qid, sm[wib], lane, false, may_defer);
+            deferred = a.dense
+                           ? walk_query<D, 1, true, EXACT>(a, qid, sm[wib], lane, false, may_defer)
+                           : walk_query<D, 1, false, EXACT>(a, qid, sm[wib], lane, false, may_defer);
         else
-            deferred = a.dense ? walk_query<D, 2, true>(a, qid, sm[wib], lane, false, may_defer)
-                               : walk_query<D, 2, false>(a, qid, sm[wib], lane, false, may_defer);
+            deferred = a.dense
+                           ? walk_query<D, 2, true, EXACT>(a, qid, sm[wib], lane, false, may_defer)
+                           : walk_query<D, 2, false, EXACT>(a, qid, sm[wib], lane, false, may_defer);
         if (deferred && lane == 0) g.heavy_list[atomicAdd(g.heavy_count, 1u)] = (unsigned int)qi;
         next = __shfl_sync(FULL, next, 0);
     }
 }
 
-template <int D>
+template <int D, bool EXACT>
 __global__ void __launch_bounds__(kThreads, 1) batch_heavy_kernel(const BatchArgs g)
 {
     __shared__ CoopSmem sm;
@@ -1204,14 +1210,14 @@ __global__ void __launch_bounds__(kThreads, 1) batch_heavy_kernel(const BatchArg
         const long long qid = (long long)(qi - __ldg(g.qoff + i));
         if (a.k <= 32) {
             if (a.dense)
-                coop_query<D, 1, true>(a, qid, sm);
+                coop_query<D, 1, true, EXACT>(a, qid, sm);
             else
-                coop_query<D, 1, false>(a, qid, sm);
+                coop_query<D, 1, false, EXACT>(a, qid, sm);
         } else {
             if (a.dense)
-                coop_query<D, 2, true>(a, qid, sm);
+                coop_query<D, 2, true, EXACT>(a, qid, sm);
             else
-                coop_query<D, 2, false>(a, qid, sm);
+                coop_query<D, 2, false, EXACT>(a, qid, sm);
         }
     }
 }
@@ -1229,50 +1235,68 @@ int blocks_per_sm(Kernel k, int& cache)
     return cache;
 }
 
-template <int D, int NS, bool DENSE>
+template <int D, int NS, bool DENSE, bool EXACT>
 cudaError_t launch_one(const QueryArgs& a, int sms, cudaStream_t s)
 {
     static int per_sm = 0, per_sm_heavy = 0;
-    long long blocks = (long long)sms * blocks_per_sm(query_kernel<D, NS, DENSE>, per_sm);
+    long long blocks = (long long)sms * blocks_per_sm(query_kernel<D, NS, DENSE, EXACT>, per_sm);
     const long long need = (a.m + kWarps - 1) / kWarps;
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
-    query_kernel<D, NS, DENSE><<<(int)blocks, kThreads, 0, s>>>(a);
+    query_kernel<D, NS, DENSE, EXACT><<<(int)blocks, kThreads, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || a.heavy_list == nullptr) return e;
-    long long hb = (long long)sms * blocks_per_sm(heavy_kernel<D, NS, DENSE>, per_sm_heavy);
+    long long hb =
+        (long long)sms * blocks_per_sm(heavy_kernel<D, NS, DENSE, EXACT>, per_sm_heavy);
     if (hb > a.m) hb = a.m;
     if (hb < 1) hb = 1;
-    heavy_kernel<D, NS, DENSE><<<(int)hb, kThreads, 0, s>>>(a);
+    heavy_kernel<D, NS, DENSE, EXACT><<<(int)hb, kThreads, 0, s>>>(a);
     count_launches(1);
     return cudaGetLastError();
+}
+
+template <int D, bool EXACT>
+cudaError_t launch_batch_one(const BatchArgs& g, int sms, cudaStream_t s)
+{
+    static int per_sm = 0, per_sm_heavy = 0;
+    long long blocks = (long long)sms * blocks_per_sm(batch_query_kernel<D, EXACT>, per_sm);
+    const long long need = (long long)((g.total + kWarps - 1) / kWarps);
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    batch_query_kernel<D, EXACT><<<(int)blocks, kThreads, 0, s>>>(g);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || g.heavy_list == nullptr) return e;
+    long long hb = (long long)sms * blocks_per_sm(batch_heavy_kernel<D, EXACT>, per_sm_heavy);
+    if (hb > (long long)g.total) hb = (long long)g.total;
+    if (hb < 1) hb = 1;
+    batch_heavy_kernel<D, EXACT><<<(int)hb, kThreads, 0, s>>>(g);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <int D, bool EXACT>
+cudaError_t launch_rule(const QueryArgs& a, int sms, cudaStream_t s)
+{
+    const bool two = a.k > 32;
+    if (a.dense)
+        return two ? launch_one<D, 2, true, EXACT>(a, sms, s)
+                   : launch_one<D, 1, true, EXACT>(a, sms, s);
+    return two ? launch_one<D, 2, false, EXACT>(a, sms, s)
+               : launch_one<D, 1, false, EXACT>(a, sms, s);
+}
+
+// The stop rule is a compile-time choice: the kernels of the paper's rule
+// carry no code of the certified one (whose registers would spill theirs).
+template <int D>
+cudaError_t launch_d(const QueryArgs& a, int sms, cudaStream_t s)
+{
+    return a.exact ? launch_rule<D, true>(a, sms, s) : launch_rule<D, false>(a, sms, s);
 }
 
 template <int D>
 cudaError_t launch_batch_d(const BatchArgs& g, int sms, cudaStream_t s)
 {
-    static int per_sm = 0, per_sm_heavy = 0;
-    long long blocks = (long long)sms * blocks_per_sm(batch_query_kernel<D>, per_sm);
-    const long long need = (long long)((g.total + kWarps - 1) / kWarps);
-    if (blocks > need) blocks = need;
-    if (blocks < 1) blocks = 1;
-    batch_query_kernel<D><<<(int)blocks, kThreads, 0, s>>>(g);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || g.heavy_list == nullptr) return e;
-    long long hb = (long long)sms * blocks_per_sm(batch_heavy_kernel<D>, per_sm_heavy);
-    if (hb > (long long)g.total) hb = (long long)g.total;
-    if (hb < 1) hb = 1;
-    batch_heavy_kernel<D><<<(int)hb, kThreads, 0, s>>>(g);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-template <int D>
-cudaError_t launch_d(const QueryArgs& a, int sms, cudaStream_t s)
-{
-    const bool two = a.k > 32;
-    if (a.dense) return two ? launch_one<D, 2, true>(a, sms, s) : launch_one<D, 1, true>(a, sms, s);
-    return two ? launch_one<D, 2, false>(a, sms, s) : launch_one<D, 1, false>(a, sms, s);
+    return g.exact ? launch_batch_one<D, true>(g, sms, s) : launch_batch_one<D, false>(g, sms, s);
 }
 
 }  // namespace qk
