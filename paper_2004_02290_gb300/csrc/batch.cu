@@ -743,6 +743,8 @@ struct Layout {
     std::vector<int> group_qoff;              // first qoff entry of each group
     std::vector<int> group_count;
     std::vector<int> group_d;
+    std::vector<int> group_ns;     // 1: k <= 32, 2: k > 32
+    std::vector<int> group_dense;  // dense tables
     std::vector<unsigned long long> group_total;
 };
 
@@ -772,15 +774,22 @@ knn_status plan_layout(const ghn_batch* b, const float* const* queries, const in
             return KNN_EINVAL;
         }
     }
-    for (int dim = 1; dim <= kMaxD; ++dim) {
+    // one group per (dimension, buffer width, table kind): each launches a
+    // kernel specialised for all three
+    for (int key = 0; key < 4 * (kMaxD + 1); ++key) {
+        const int dim = key / 4, ns = (key & 2) ? 2 : 1, dense = key & 1;
         std::vector<int> members;
         for (int i = 0; i < b->count; ++i)
-            if (b->info[i].d == dim && m[i] > 0) members.push_back(i);
+            if (b->info[i].d == dim && m[i] > 0 && (k[i] > 32 ? 2 : 1) == ns &&
+                (b->proto[i].dense ? 1 : 0) == dense)
+                members.push_back(i);
         if (members.empty()) continue;
         lay.group_first.push_back((int)lay.args.size());
         lay.group_qoff.push_back((int)lay.qoff.size());
         lay.group_count.push_back((int)members.size());
         lay.group_d.push_back(dim);
+        lay.group_ns.push_back(ns);
+        lay.group_dense.push_back(dense);
         unsigned long long acc = 0ull;
         for (int i : members) {
             QueryArgs a = b->proto[i];
@@ -844,6 +853,8 @@ knn_status make_plan(const ghn_batch* b, Layout& lay, cudaStream_t s, ghn_plan* 
         ba.heavy_cursor = ba.heavy_count + 1;
         ba.heavy_list = heavy + hoff;
         ba.exact = lay.args[lay.group_first[g]].exact;  // one rule for the whole call
+        ba.ns = lay.group_ns[g];
+        ba.dense = lay.group_dense[g];
         hoff += lay.group_total[g];
         p->groups.push_back(ba);
     }

@@ -152,8 +152,10 @@ struct QueryArgs {
 
 cudaError_t launch_query(const QueryArgs& a, int num_sms, cudaStream_t s);
 
-// A group of indexes of one dimension queried in one persistent launch: the
-// queries of index i are the group's queries qoff[i] .. qoff[i+1]-1.
+// A group of indexes queried in one persistent launch: the queries of index i
+// are the group's queries qoff[i] .. qoff[i+1]-1.  Every index of a group has
+// the same dimension, buffer width (ns: 1 for k <= 32, 2 above), table kind
+// and stop rule.
 struct BatchArgs {
     const QueryArgs* args;           // device: one per index of the group
     const unsigned long long* qoff;  // device: count + 1 prefix offsets
@@ -165,6 +167,8 @@ struct BatchArgs {
     unsigned int* heavy_count;       // zero at launch
     unsigned int* heavy_cursor;      // zero at launch
     int exact;                       // certified stop for every index of the group
+    int ns;                          // 1: k <= 32 for every index; 2: k > 32
+    int dense;                       // every index has a dense table
 };
 
 cudaError_t launch_batch_query(const BatchArgs& g, int num_sms, cudaStream_t s);

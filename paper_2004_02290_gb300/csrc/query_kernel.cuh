@@ -759,10 +759,11 @@ struct WarpSmem {
 
 // One query by one warp.  Returns true when the query was deferred to the
 // cooperative kernel (nothing written); otherwise its outputs are written.
-template <int D, int NS, bool DENSE, bool EXACT>
+template <int D, int NS, bool DENSE, bool EXACT, bool COUNT>
 __device__ __forceinline__ bool walk_query(const QueryArgs& a, long long qid, WarpSmem& sm,
-                                           int lane, bool counting, bool may_defer)
+                                           int lane, bool may_defer)
 {
+    constexpr bool counting = COUNT;  // the exhaustive counting walk of knn_query_stats
     unsigned long long hmask = 0ull;
     if constexpr (!DENSE) hmask = a.gdev->hmask;
     Query<D> s;
@@ -891,15 +892,14 @@ __device__ __forceinline__ bool walk_query(const QueryArgs& a, long long qid, Wa
     return false;
 }
 
-template <int D, int NS, bool DENSE, bool EXACT>
+template <int D, int NS, bool DENSE, bool EXACT, bool COUNT>
 __global__ void __launch_bounds__(kThreads, (MinBlocks<D, NS>::value))
     query_kernel(const QueryArgs a)
 {
     __shared__ WarpSmem sm[kWarps];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const bool counting = a.stats != nullptr;
-    const bool may_defer = !counting && a.heavy_list != nullptr;
+    const bool may_defer = !COUNT && a.heavy_list != nullptr;
 
     // the next query is claimed one query ahead, so the atomic's latency
     // overlaps the current query's work
@@ -910,7 +910,7 @@ __global__ void __launch_bounds__(kThreads, (MinBlocks<D, NS>::value))
         const unsigned long long qi = next;
         if (lane == 0) next = atomicAdd(a.counter, 1ull);
         const long long qid = a.order ? (long long)a.order[qi] : (long long)qi;
-        if (walk_query<D, NS, DENSE, EXACT>(a, qid, sm[wib], lane, counting, may_defer) &&
+        if (walk_query<D, NS, DENSE, EXACT, COUNT>(a, qid, sm[wib], lane, may_defer) &&
             lane == 0) {
             // too much work for one warp: the cooperative kernel takes it
             a.heavy_list[atomicAdd(a.heavy_count, 1u)] = (unsigned int)qid;
@@ -1161,8 +1161,11 @@ __device__ __forceinline__ int group_index(const unsigned long long* qoff, int c
     return lo;
 }
 
-template <int D, bool EXACT>
-__global__ void __launch_bounds__(kThreads, (MinBlocks<D, 1>::value))
+// Every index of a group shares the dimension, the buffer width (k <= 32 or
+// not), the table kind and the stop rule, so the walk is specialised as in
+// the single-index kernel.
+template <int D, int NS, bool DENSE, bool EXACT>
+__global__ void __launch_bounds__(kThreads, (MinBlocks<D, NS>::value))
     batch_query_kernel(const BatchArgs g)
 {
     __shared__ WarpSmem sm[kWarps];
@@ -1178,21 +1181,14 @@ __global__ void __launch_bounds__(kThreads, (MinBlocks<D, 1>::value))
         const int i = group_index(g.qoff, g.count, qi);
         const QueryArgs& a = g.args[i];
         const long long qid = (long long)(qi - __ldg(g.qoff + i));
-        bool deferred;
-        if (a.k <= 32)
-            deferred = a.dense
-                           ? walk_query<D, 1, true, EXACT>(a, qid, sm[wib], lane, false, may_defer)
-                           : walk_query<D, 1, false, EXACT>(a, qid, sm[wib], lane, false, may_defer);
-        else
-            deferred = a.dense
-                           ? walk_query<D, 2, true, EXACT>(a, qid, sm[wib], lane, false, may_defer)
-                           : walk_query<D, 2, false, EXACT>(a, qid, sm[wib], lane, false, may_defer);
+        const bool deferred =
+            walk_query<D, NS, DENSE, EXACT, false>(a, qid, sm[wib], lane, may_defer);
         if (deferred && lane == 0) g.heavy_list[atomicAdd(g.heavy_count, 1u)] = (unsigned int)qi;
         next = __shfl_sync(FULL, next, 0);
     }
 }
 
-template <int D, bool EXACT>
+template <int D, int NS, bool DENSE, bool EXACT>
 __global__ void __launch_bounds__(kThreads, 1) batch_heavy_kernel(const BatchArgs g)
 {
     __shared__ CoopSmem sm;
@@ -1208,17 +1204,7 @@ __global__ void __launch_bounds__(kThreads, 1) batch_heavy_kernel(const BatchArg
         const int i = group_index(g.qoff, g.count, qi);
         const QueryArgs& a = g.args[i];
         const long long qid = (long long)(qi - __ldg(g.qoff + i));
-        if (a.k <= 32) {
-            if (a.dense)
-                coop_query<D, 1, true, EXACT>(a, qid, sm);
-            else
-                coop_query<D, 1, false, EXACT>(a, qid, sm);
-        } else {
-            if (a.dense)
-                coop_query<D, 2, true, EXACT>(a, qid, sm);
-            else
-                coop_query<D, 2, false, EXACT>(a, qid, sm);
-        }
+        coop_query<D, NS, DENSE, EXACT>(a, qid, sm);
     }
 }
 
@@ -1235,17 +1221,18 @@ int blocks_per_sm(Kernel k, int& cache)
     return cache;
 }
 
-template <int D, int NS, bool DENSE, bool EXACT>
+template <int D, int NS, bool DENSE, bool EXACT, bool COUNT>
 cudaError_t launch_one(const QueryArgs& a, int sms, cudaStream_t s)
 {
     static int per_sm = 0, per_sm_heavy = 0;
-    long long blocks = (long long)sms * blocks_per_sm(query_kernel<D, NS, DENSE, EXACT>, per_sm);
+    long long blocks =
+        (long long)sms * blocks_per_sm(query_kernel<D, NS, DENSE, EXACT, COUNT>, per_sm);
     const long long need = (a.m + kWarps - 1) / kWarps;
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
-    query_kernel<D, NS, DENSE, EXACT><<<(int)blocks, kThreads, 0, s>>>(a);
+    query_kernel<D, NS, DENSE, EXACT, COUNT><<<(int)blocks, kThreads, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || a.heavy_list == nullptr) return e;
+    if (e != cudaSuccess || a.heavy_list == nullptr || COUNT) return e;
     long long hb =
         (long long)sms * blocks_per_sm(heavy_kernel<D, NS, DENSE, EXACT>, per_sm_heavy);
     if (hb > a.m) hb = a.m;
@@ -1255,48 +1242,63 @@ cudaError_t launch_one(const QueryArgs& a, int sms, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <int D, bool EXACT>
+template <int D, int NS, bool DENSE, bool EXACT>
 cudaError_t launch_batch_one(const BatchArgs& g, int sms, cudaStream_t s)
 {
     static int per_sm = 0, per_sm_heavy = 0;
-    long long blocks = (long long)sms * blocks_per_sm(batch_query_kernel<D, EXACT>, per_sm);
+    long long blocks =
+        (long long)sms * blocks_per_sm(batch_query_kernel<D, NS, DENSE, EXACT>, per_sm);
     const long long need = (long long)((g.total + kWarps - 1) / kWarps);
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
-    batch_query_kernel<D, EXACT><<<(int)blocks, kThreads, 0, s>>>(g);
+    batch_query_kernel<D, NS, DENSE, EXACT><<<(int)blocks, kThreads, 0, s>>>(g);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || g.heavy_list == nullptr) return e;
-    long long hb = (long long)sms * blocks_per_sm(batch_heavy_kernel<D, EXACT>, per_sm_heavy);
+    long long hb =
+        (long long)sms * blocks_per_sm(batch_heavy_kernel<D, NS, DENSE, EXACT>, per_sm_heavy);
     if (hb > (long long)g.total) hb = (long long)g.total;
     if (hb < 1) hb = 1;
-    batch_heavy_kernel<D, EXACT><<<(int)hb, kThreads, 0, s>>>(g);
+    batch_heavy_kernel<D, NS, DENSE, EXACT><<<(int)hb, kThreads, 0, s>>>(g);
     count_launches(1);
     return cudaGetLastError();
 }
 
-template <int D, bool EXACT>
+template <int D, bool EXACT, bool COUNT>
 cudaError_t launch_rule(const QueryArgs& a, int sms, cudaStream_t s)
 {
     const bool two = a.k > 32;
     if (a.dense)
-        return two ? launch_one<D, 2, true, EXACT>(a, sms, s)
-                   : launch_one<D, 1, true, EXACT>(a, sms, s);
-    return two ? launch_one<D, 2, false, EXACT>(a, sms, s)
-               : launch_one<D, 1, false, EXACT>(a, sms, s);
+        return two ? launch_one<D, 2, true, EXACT, COUNT>(a, sms, s)
+                   : launch_one<D, 1, true, EXACT, COUNT>(a, sms, s);
+    return two ? launch_one<D, 2, false, EXACT, COUNT>(a, sms, s)
+               : launch_one<D, 1, false, EXACT, COUNT>(a, sms, s);
 }
 
-// The stop rule is a compile-time choice: the kernels of the paper's rule
-// carry no code of the certified one (whose registers would spill theirs).
+// The stop rule and the counting walk are compile-time choices: the kernels
+// of the paper's rule carry no code of the certified rule or of the counting
+// walk (whose registers would spill theirs).  The counting walk exists for
+// the paper's rule only.
 template <int D>
 cudaError_t launch_d(const QueryArgs& a, int sms, cudaStream_t s)
 {
-    return a.exact ? launch_rule<D, true>(a, sms, s) : launch_rule<D, false>(a, sms, s);
+    if (a.stats) return a.exact ? cudaErrorInvalidValue : launch_rule<D, false, true>(a, sms, s);
+    return a.exact ? launch_rule<D, true, false>(a, sms, s) : launch_rule<D, false, false>(a, sms, s);
+}
+
+template <int D, bool EXACT>
+cudaError_t launch_batch_rule(const BatchArgs& g, int sms, cudaStream_t s)
+{
+    if (g.dense)
+        return g.ns == 2 ? launch_batch_one<D, 2, true, EXACT>(g, sms, s)
+                         : launch_batch_one<D, 1, true, EXACT>(g, sms, s);
+    return g.ns == 2 ? launch_batch_one<D, 2, false, EXACT>(g, sms, s)
+                     : launch_batch_one<D, 1, false, EXACT>(g, sms, s);
 }
 
 template <int D>
 cudaError_t launch_batch_d(const BatchArgs& g, int sms, cudaStream_t s)
 {
-    return g.exact ? launch_batch_one<D, true>(g, sms, s) : launch_batch_one<D, false>(g, sms, s);
+    return g.exact ? launch_batch_rule<D, true>(g, sms, s) : launch_batch_rule<D, false>(g, sms, s);
 }
 
 }  // namespace qk

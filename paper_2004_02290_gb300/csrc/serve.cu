@@ -49,6 +49,7 @@ using ghn::QueryArgs;
 namespace {
 
 constexpr int kQuery = 0, kBuild = 1, kDrop = 2;
+constexpr int kGroups = 4 * (ghn::kMaxD + 1);  // launch groups: (d, buffer width, table kind)
 
 long long clock_ns()
 {
@@ -83,6 +84,7 @@ struct Ticket {
     float* dist2 = nullptr;
     void* pred = nullptr;
     const ghn_index* x = nullptr;  // set at dispatch
+    int group = 0;                 // launch group within its batch
     // build request
     const float* points = nullptr;
     const void* labels = nullptr;
@@ -169,8 +171,8 @@ struct ghn_server {
     std::thread dispatcher, completer, builder;
 
     size_t cap_args() const { return align16((size_t)cfg.max_batch_requests * sizeof(QueryArgs)); }
-    size_t cap_qoff() const { return align16(((size_t)cfg.max_batch_requests + ghn::kMaxD) * 8); }
-    size_t cap_cnt() const { return align16((size_t)ghn::kMaxD * 32); }
+    size_t cap_qoff() const { return align16(((size_t)cfg.max_batch_requests + kGroups) * 8); }
+    size_t cap_cnt() const { return align16((size_t)kGroups * 32); }
     size_t meta_bytes() const
     {
         return cap_args() + cap_qoff() + cap_cnt() +
@@ -284,9 +286,17 @@ void ghn_server::dispatch_loop()
 void ghn_server::pack_and_launch(Slot& sl)
 {
     const size_t E = sl.reqs.size();
-    // group the requests by dimension (stable: arrival order inside a group)
+    // group the requests by dimension, buffer width (k <= 32 or not) and table
+    // kind (stable: arrival order inside a group); each group is one launch of
+    // a kernel specialised for all three
+    for (auto& t : sl.reqs) {
+        QueryArgs a;
+        memset(&a, 0, sizeof(a));
+        ghn::index_query_args(t->x, a);
+        t->group = t->d * 4 + (t->k > 32 ? 2 : 0) + (a.dense ? 1 : 0);
+    }
     std::stable_sort(sl.reqs.begin(), sl.reqs.end(),
-                     [](const TicketP& a, const TicketP& b) { return a->d < b->d; });
+                     [](const TicketP& a, const TicketP& b) { return a->group < b->group; });
     sl.q_at.assign(E, 0);
     sl.o_at.assign(E, 0);
     size_t nq = 0, no = 0, nf = 0;
@@ -300,7 +310,7 @@ void ghn_server::pack_and_launch(Slot& sl)
     // compact layouts of this batch
     const size_t off_args = 0;
     const size_t off_qoff = align16(E * sizeof(QueryArgs));
-    const size_t off_cnt = off_qoff + align16((E + ghn::kMaxD) * 8);
+    const size_t off_cnt = off_qoff + align16((E + kGroups) * 8);
     const size_t off_q = off_cnt + cap_cnt();
     const size_t meta = off_q + nf * 4;
     sl.off_status = 0;
@@ -321,14 +331,16 @@ void ghn_server::pack_and_launch(Slot& sl)
     std::vector<BatchArgs> groups;
     size_t qf = 0, qoff_at = 0;
     for (size_t i = 0; i < E;) {
-        const int d = sl.reqs[i]->d;
+        const int d = sl.reqs[i]->d, key = sl.reqs[i]->group;
         size_t j = i;
         BatchArgs g{};
         g.args = da + i;
         g.qoff = dq + qoff_at;
         g.d = d;
+        g.ns = (key & 2) ? 2 : 1;
+        g.dense = key & 1;
         unsigned long long acc = 0;
-        for (; j < E && sl.reqs[j]->d == d; ++j) {
+        for (; j < E && sl.reqs[j]->group == key; ++j) {
             const Ticket& t = *sl.reqs[j];
             QueryArgs a;
             memset(&a, 0, sizeof(a));
