@@ -713,7 +713,7 @@ def run_serving(args):
     for e, (oi, od, op) in zip(qev, outs_s):
         tk = ctypes.c_int64()
         rc = lib.knn_server_submit(h, ids[e.index], e.queries.ctypes.data, e.queries.shape[0], e.k,
-                                   e.mode, oi.ctypes.data, od.ctypes.data, op.ctypes.data,
+                                   e.mode, oi.ctypes.data, od.ctypes.data, op.ctypes.data, 0,
                                    ctypes.byref(tk))
         if rc != 0:
             raise RuntimeError("submit failed")

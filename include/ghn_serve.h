@@ -110,10 +110,10 @@ int64_t knn_server_build_bytes(int64_t n, int32_t d, int32_t labels);
 knn_status knn_server_drop(ghn_server* server, int64_t index_id, int64_t* ticket);
 
 /*
- * knn_server_submit: a query request (the arguments of knn_query, without
- * flags; results as knn_query's with KNN_QUERY_CHECKED: the ticket's status
- * is KNN_EINVAL for a non-finite query and KNN_ELIMIT for one that reached
- * the layer cap).
+ * knn_server_submit: a query request (the arguments of knn_query; results as
+ * knn_query's with KNN_QUERY_CHECKED: the ticket's status is KNN_EINVAL for
+ * a non-finite query and KNN_ELIMIT for one that reached the layer cap).
+ *   flags    0 or KNN_QUERY_EXACT (the certified stop for this request).
  *   queries  host, m*d float32 of the index's d; borrowed until completion.
  *   ids      host, m*k int32; dist2 host m*k float32 or NULL; pred host m
  *            values (int32 for KNN_VOTE, float32 for KNN_MEAN / KNN_MEDIAN)
@@ -123,7 +123,7 @@ knn_status knn_server_drop(ghn_server* server, int64_t index_id, int64_t* ticket
  */
 knn_status knn_server_submit(ghn_server* server, int64_t index_id, const float* queries,
                              int64_t m, int32_t k, int32_t mode, int32_t* ids, float* dist2,
-                             void* pred, int64_t* ticket);
+                             void* pred, int32_t flags, int64_t* ticket);
 
 /*
  * knn_server_wait: wait up to timeout_us (negative: no limit) for a ticket.

@@ -49,7 +49,8 @@ using ghn::QueryArgs;
 namespace {
 
 constexpr int kQuery = 0, kBuild = 1, kDrop = 2;
-constexpr int kGroups = 4 * (ghn::kMaxD + 1);  // launch groups: (d, buffer width, table kind)
+// launch groups of a batch: (d, buffer width, table kind, stop rule)
+constexpr int kGroups = 8 * (ghn::kMaxD + 1);
 
 long long clock_ns()
 {
@@ -80,6 +81,7 @@ struct Ticket {
     int k = 0;
     int mode = -1;
     int d = 0;
+    int exact = 0;  // certified stop
     int32_t* ids = nullptr;
     float* dist2 = nullptr;
     void* pred = nullptr;
@@ -293,7 +295,7 @@ void ghn_server::pack_and_launch(Slot& sl)
         QueryArgs a;
         memset(&a, 0, sizeof(a));
         ghn::index_query_args(t->x, a);
-        t->group = t->d * 4 + (t->k > 32 ? 2 : 0) + (a.dense ? 1 : 0);
+        t->group = t->d * 8 + (t->k > 32 ? 4 : 0) + (a.dense ? 2 : 0) + t->exact;
     }
     std::stable_sort(sl.reqs.begin(), sl.reqs.end(),
                      [](const TicketP& a, const TicketP& b) { return a->group < b->group; });
@@ -337,8 +339,9 @@ void ghn_server::pack_and_launch(Slot& sl)
         g.args = da + i;
         g.qoff = dq + qoff_at;
         g.d = d;
-        g.ns = (key & 2) ? 2 : 1;
-        g.dense = key & 1;
+        g.ns = (key & 4) ? 2 : 1;
+        g.dense = (key >> 1) & 1;
+        g.exact = key & 1;
         unsigned long long acc = 0;
         for (; j < E && sl.reqs[j]->group == key; ++j) {
             const Ticket& t = *sl.reqs[j];
@@ -357,6 +360,7 @@ void ghn_server::pack_and_launch(Slot& sl)
                                            sl.q_at[j])
                                  : nullptr;
             a.status = reinterpret_cast<unsigned int*>(sl.dout + sl.off_status) + j;
+            a.exact = t.exact;
             ha[j] = a;
             hq[qoff_at + (j - i)] = acc;
             acc += (unsigned long long)t.m;
@@ -688,10 +692,14 @@ knn_status knn_server_drop(ghn_server* s, int64_t index_id, int64_t* ticket)
 
 knn_status knn_server_submit(ghn_server* s, int64_t index_id, const float* queries, int64_t m,
                              int32_t k, int32_t mode, int32_t* ids, float* dist2, void* pred,
-                             int64_t* ticket)
+                             int32_t flags, int64_t* ticket)
 {
     if (!s || !ticket) {
         ghn::set_error("knn_server_submit: NULL argument");
+        return KNN_EINVAL;
+    }
+    if (flags & ~KNN_QUERY_EXACT) {
+        ghn::set_error("knn_server_submit: flags may only hold KNN_QUERY_EXACT");
         return KNN_EINVAL;
     }
     if (m < 0 || k < 1 || k > ghn::kMaxK || mode < -1 || mode > 2) {
@@ -716,6 +724,7 @@ knn_status knn_server_submit(ghn_server* s, int64_t index_id, const float* queri
     t->ids = ids;
     t->dist2 = dist2;
     t->pred = mode >= 0 ? pred : nullptr;
+    t->exact = (flags & KNN_QUERY_EXACT) ? 1 : 0;
     t->t_submit = clock_ns();
     std::lock_guard<std::mutex> lk(s->mu);
     auto it = s->indexes.find(index_id);

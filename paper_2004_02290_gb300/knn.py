@@ -141,7 +141,7 @@ def library(path: str | None = None) -> ctypes.CDLL:
         lib.knn_server_build.restype = i32
         lib.knn_server_drop.argtypes = [vp, i64, pi64]
         lib.knn_server_drop.restype = i32
-        lib.knn_server_submit.argtypes = [vp, i64, vp, i64, i32, i32, vp, vp, vp, pi64]
+        lib.knn_server_submit.argtypes = [vp, i64, vp, i64, i32, i32, vp, vp, vp, i32, pi64]
         lib.knn_server_submit.restype = i32
         lib.knn_server_wait.argtypes = [vp, i64, i64, ctypes.POINTER(knn_ticket_info)]
         lib.knn_server_wait.restype = i32
@@ -558,8 +558,11 @@ class Server:
         return t.value
 
     def submit(self, index_id: int, queries: np.ndarray, k: int, mode: int = KNN_NONE,
-               want_dist2: bool = True):
-        """Queue a query request (host arrays); returns (ticket, ids, dist2, pred)."""
+               want_dist2: bool = True, flags: int = 0):
+        """Queue a query request (host arrays); returns (ticket, ids, dist2, pred).
+
+        flags: 0 or KNN_QUERY_EXACT (the certified stop for this request).
+        """
         q = np.ascontiguousarray(queries, np.float32)
         m = int(q.shape[0])
         ids = np.empty((m, k), np.int32)
@@ -571,7 +574,7 @@ class Server:
         _check(library().knn_server_submit(
             self._h, index_id, q.ctypes.data, m, k, mode, ids.ctypes.data,
             d2.ctypes.data if d2 is not None else None,
-            pred.ctypes.data if pred is not None else None, ctypes.byref(t)))
+            pred.ctypes.data if pred is not None else None, flags, ctypes.byref(t)))
         with self._klock:
             self._keep[t.value] = (q, ids, d2, pred)
         return t.value, ids, d2, pred

@@ -140,7 +140,7 @@ def test_server_rejects_bad_arguments_on_the_host(lib):
     bad = knn.knn_server_config(0, -5, 0, 0, 0, 0, 0)
     assert lib.knn_server_create(ctypes.byref(bad), ctypes.byref(h)) == knn.KNN_EINVAL
     t = ctypes.c_int64()
-    assert lib.knn_server_submit(None, 1, None, 0, 5, -1, None, None, None,
+    assert lib.knn_server_submit(None, 1, None, 0, 5, -1, None, None, None, 0,
                                  ctypes.byref(t)) == knn.KNN_EINVAL
     assert lib.knn_server_wait(None, 1, 0, None) == knn.KNN_EINVAL
     assert lib.knn_server_drop(None, 1, ctypes.byref(t)) == knn.KNN_EINVAL

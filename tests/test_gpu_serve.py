@@ -230,3 +230,20 @@ def test_borrowed_index_answers_plain_queries(server_with_indexes):
     assert np.array_equal(ids, ids2)
     with pytest.raises(knn.KnnError):
         srv.index(987654)
+
+
+def test_exact_requests_equal_exhaustive_in_the_mix(server_with_indexes):
+    """Requests with the certified stop share batches with the paper's rule."""
+    srv, ids_of, data = server_with_indexes
+    reqs = _requests(24, seed=5)
+    tickets = []
+    for j, (i, q, k, mode) in enumerate(reqs):
+        flags = knn.KNN_QUERY_EXACT if j % 2 else 0
+        tickets.append((flags, srv.submit(ids_of[i], q, k, mode, flags=flags)))
+    grids = [oracle.Grid(x, lab, INDEXES[i][2]) for i, (x, lab) in enumerate(data)]
+    for (flags, (t, ids, d2, pred)), (i, q, k, mode) in zip(tickets, reqs):
+        assert srv.wait(t).status == knn.KNN_OK
+        rule = oracle.RULE_EXACT if flags else oracle.RULE_PAPER
+        _same((ids, d2, pred), grids[i].query(q, k, mode, rule=rule))
+    with pytest.raises(knn.KnnError):
+        srv.submit(ids_of[0], np.zeros((1, 2), np.float32), 3, flags=knn.KNN_QUERY_SORTED)
