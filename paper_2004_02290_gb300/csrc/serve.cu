@@ -408,6 +408,12 @@ void ghn_server::complete_loop()
         int batch_status = sl.launch_status;
         if (batch_status == KNN_OK && cudaEventSynchronize(sl.event) != cudaSuccess)
             batch_status = KNN_ECUDA;
+        if (batch_status != KNN_OK) {
+            // whatever was queued before the failure finishes before the
+            // slot's buffers are reused
+            cudaStreamSynchronize(sl.stream);
+            cudaGetLastError();
+        }
         std::vector<int> status(sl.reqs.size(), batch_status);
         long long nq = 0;
         if (batch_status == KNN_OK) {
@@ -509,6 +515,18 @@ void ghn_server::build_loop()
 // ---------------------------------------------------------------------------
 
 namespace {
+
+// True for device (or managed) memory; host, pinned and NULL pointers are not.
+bool on_device(const void* p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
 
 void fill_info(const Ticket& t, knn_ticket_info* info)
 {
@@ -708,6 +726,10 @@ knn_status knn_server_submit(ghn_server* s, int64_t index_id, const float* queri
     }
     if (m > 0 && (!queries || !ids || (mode >= 0 && !pred))) {
         ghn::set_error("knn_server_submit: queries, ids (and pred for a prediction) are required");
+        return KNN_EINVAL;
+    }
+    if (m > 0 && (on_device(queries) || on_device(ids) || on_device(dist2) || on_device(pred))) {
+        ghn::set_error("knn_server_submit: queries and outputs must be host memory");
         return KNN_EINVAL;
     }
     if (m > s->cfg.max_batch_queries || m * (int64_t)k > s->cfg.max_batch_outputs) {

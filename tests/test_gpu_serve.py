@@ -247,3 +247,13 @@ def test_exact_requests_equal_exhaustive_in_the_mix(server_with_indexes):
         _same((ids, d2, pred), grids[i].query(q, k, mode, rule=rule))
     with pytest.raises(knn.KnnError):
         srv.submit(ids_of[0], np.zeros((1, 2), np.float32), 3, flags=knn.KNN_QUERY_SORTED)
+
+
+def test_device_buffers_are_rejected(server_with_indexes):
+    srv, ids_of, _ = server_with_indexes
+    q = torch.zeros((4, 2), dtype=torch.float32, device="cuda")
+    ids = torch.zeros((4, 3), dtype=torch.int32, device="cuda")
+    t = knn.ctypes.c_int64()
+    rc = knn.library().knn_server_submit(srv._h, ids_of[0], q.data_ptr(), 4, 3, -1,
+                                         ids.data_ptr(), None, None, 0, knn.ctypes.byref(t))
+    assert rc == knn.KNN_EINVAL
