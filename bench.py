@@ -417,8 +417,8 @@ def recall_vs_exact(knn, idx, q, w, ids_paper, stream):
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     with torch.cuda.stream(stream):
         ev[0].record(stream)
-    ex_ids, _, _ = knn.knn_query(idx, q, w.k, knn.KNN_NONE, flags=knn.KNN_QUERY_EXACT,
-                                 stream=stream)
+    ex_ids, ex_d2, _ = knn.knn_query(idx, q, w.k, knn.KNN_NONE, flags=knn.KNN_QUERY_EXACT,
+                                     stream=stream)
     with torch.cuda.stream(stream):
         ev[1].record(stream)
     ev[1].synchronize()
@@ -429,7 +429,13 @@ def recall_vs_exact(knn, idx, q, w, ids_paper, stream):
         rb = rb[rb >= 0]
         hit += np.intersect1d(ra, rb, assume_unique=True).size
     total = int((b >= 0).sum())
+    # distance recall: returned squared distances within the exact k-th one
+    _, d2_paper, _ = knn.knn_query(idx, q, w.k, knn.KNN_NONE, stream=stream)
+    dp = d2_paper.cpu().numpy()
+    kth = ex_d2.cpu().numpy()[:, -1:]
+    within = int((dp <= kth).sum())
     return {"recall": hit / max(1, total),
+            "distance_recall": within / max(1, dp.size),
             "queries_with_all_k": float(np.mean([np.array_equal(np.sort(ra), np.sort(rb))
                                                  for ra, rb in zip(a, b)])),
             "exact_query_ms": ev[0].elapsed_time(ev[1])}

@@ -15,5 +15,6 @@ from .oracle import (  # noqa: F401
     count_cells,
     library,
     measure_cells,
+    recall,
     shell_count,
 )

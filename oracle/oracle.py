@@ -265,3 +265,20 @@ def count_cells(points, w: float) -> int:
     if u < 0:
         raise ValueError("count_cells failed")
     return int(u)
+
+
+def recall(grid: "Grid", points, queries, k: int):
+    """Recall of the paper's stop rule against exhaustive KNN (Sec. III.B notes
+    that the exploration may miss true neighbours): (recall@k, distance recall).
+
+    recall@k: the share of the exact k neighbours, under (distance, index)
+    order, that the walk returned.  Distance recall: the share of returned
+    squared distances that are at most the exact k-th one.  Reported, not
+    pinned: the paper's accuracy tables need its datasets.
+    """
+    ids, d2, _ = grid.query(queries, k, -1)
+    e_ids, e_d2 = brute_force(points, queries, k)
+    hit = sum(np.intersect1d(a[a >= 0], b[b >= 0]).size for a, b in zip(ids, e_ids))
+    total = int((e_ids >= 0).sum())
+    within = int((d2 <= e_d2[:, -1:]).sum())
+    return hit / max(1, total), within / max(1, d2.size)

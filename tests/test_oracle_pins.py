@@ -503,3 +503,12 @@ def test_exact_rule_stops_once_certified():
     _, _, _, st = g.query(np.array([[39.95, 20.5]], np.float32), 1, -1, stats=True,
                           rule=oracle.RULE_EXACT)
     assert st[0, 0] == 2
+
+
+def test_recall_is_reported_and_exact_when_one_cell_holds_everything():
+    """Recall of the paper's rule against exhaustive KNN (reported, not pinned):
+    a value in [0, 1]; exactly 1 when a single cell holds every point."""
+    x, lab, q = wl.uniform(800, 60, 3, seed=31)
+    r, dr = oracle.recall(oracle.Grid(x, lab, 0.08), x, q, 10)
+    assert 0.0 <= r <= 1.0 and 0.0 <= dr <= 1.0 and dr >= r - 1e-12
+    assert oracle.recall(oracle.Grid(x, lab, 10.0), x, q, 10) == (1.0, 1.0)
