@@ -713,24 +713,44 @@ def run_serving(args):
         outs_s.append((np.empty((m, e.k), np.int32), np.empty((m, e.k), np.float32), np.empty(m, pdt)))
         outs_p.append((np.empty((m, e.k), np.int32), np.empty((m, e.k), np.float32), np.empty(m, pdt)))
     h = srv._h
-    tickets = []
-    b0 = srv.stats().batches
-    t_start = time.monotonic_ns()
-    for e, (oi, od, op) in zip(qev, outs_s):
-        tk = ctypes.c_int64()
-        rc = lib.knn_server_submit(h, ids[e.index], e.queries.ctypes.data, e.queries.shape[0], e.k,
-                                   e.mode, oi.ctypes.data, od.ctypes.data, op.ctypes.data, 0,
-                                   ctypes.byref(tk))
+    nreq = len(qev)
+    c_ = ctypes
+    a_iid = (c_.c_int64 * nreq)(*[ids[e.index] for e in qev])
+    a_q = (c_.c_void_p * nreq)(*[e.queries.ctypes.data for e in qev])
+    a_m = (c_.c_int64 * nreq)(*[e.queries.shape[0] for e in qev])
+    a_k = (c_.c_int32 * nreq)(*[e.k for e in qev])
+    a_md = (c_.c_int32 * nreq)(*[e.mode for e in qev])
+    a_i = (c_.c_void_p * nreq)(*[o[0].ctypes.data for o in outs_s])
+    a_d = (c_.c_void_p * nreq)(*[o[1].ctypes.data for o in outs_s])
+    a_p = (c_.c_void_p * nreq)(*[o[2].ctypes.data for o in outs_s])
+    a_t = (c_.c_int64 * nreq)()
+    st_pre = srv.stats()
+    b0 = st_pre.batches
+    t_start = t_cap0 = time.monotonic_ns()
+    chunk = 1024  # requests per submission call: the server starts on the first chunk
+    for c0 in range(0, nreq, chunk):
+        cn = min(chunk, nreq - c0)
+
+        def at(arr, t):
+            return c_.cast(c_.byref(arr, c0 * c_.sizeof(t)), c_.POINTER(t))
+
+        rc = lib.knn_server_submit_many(h, cn, at(a_iid, c_.c_int64), at(a_q, c_.c_void_p),
+                                        at(a_m, c_.c_int64), at(a_k, c_.c_int32),
+                                        at(a_md, c_.c_int32), at(a_i, c_.c_void_p),
+                                        at(a_d, c_.c_void_p), at(a_p, c_.c_void_p), None,
+                                        at(a_t, c_.c_int64))
         if rc != 0:
-            raise RuntimeError("submit failed")
-        tickets.append(tk.value)
+            raise RuntimeError("submit failed: " + lib.knn_last_error().decode())
+    tickets = list(a_t)
+    t_submitted = time.monotonic_ns()
     info = knn.knn_ticket_info()
     t_end = t_start
     for tk in tickets:
         lib.knn_server_wait(h, tk, -1, ctypes.byref(info))
         t_end = max(t_end, info.t_done_ns)
     served_s = (t_end - t_start) * 1e-9
-    cap_batches = srv.stats().batches - b0
+    cap_stats = srv.stats()
+    cap_batches = cap_stats.batches - b0
     launches = knn.knn_kernel_launches() - l0
     clocks = sampler.stop()
 
@@ -793,7 +813,12 @@ def run_serving(args):
                   "poisson": {"p50_ms": _pct(plat, 50), "p99_ms": _pct(plat, 99),
                               "mean_ms": float(np.mean(plat))}},
         "capacity": {"served_req_s": len(qev) / served_s, "batches": int(cap_batches),
-                     "requests_per_batch": len(qev) / max(1, cap_batches)},
+                     "requests_per_batch": len(qev) / max(1, cap_batches),
+                     "submit_ms": (t_submitted - t_cap0) * 1e-6,
+                     "host_ms_total": {
+                         "pack_launch": (cap_stats.pack_ns - st_pre.pack_ns) * 1e-6,
+                         "wait_gpu": (cap_stats.wait_ns - st_pre.wait_ns) * 1e-6,
+                         "scatter": (cap_stats.scatter_ns - st_pre.scatter_ns) * 1e-6}},
         "speedup_vs_plain": cap_served / cap_plain,
         "identical_to_plain": bool(identical),
         "e2e": {"value": cap_served, "unit": UNIT, "h2d_bytes_per_step": h2d,

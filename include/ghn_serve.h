@@ -72,6 +72,9 @@ typedef struct {
     int64_t inflight_batches;
     int64_t max_batch_requests_seen;
     int64_t max_batch_queries_seen;
+    int64_t pack_ns;          /* host time packing and launching batches */
+    int64_t wait_ns;          /* host time waiting for batches to finish */
+    int64_t scatter_ns;       /* host time copying results to the callers' buffers */
 } knn_server_stats_t;
 
 /*
@@ -124,6 +127,18 @@ knn_status knn_server_drop(ghn_server* server, int64_t index_id, int64_t* ticket
 knn_status knn_server_submit(ghn_server* server, int64_t index_id, const float* queries,
                              int64_t m, int32_t k, int32_t mode, int32_t* ids, float* dist2,
                              void* pred, int32_t flags, int64_t* ticket);
+
+/*
+ * knn_server_submit_many: `count` query requests in one call (host arrays of
+ * count entries, each as knn_server_submit's argument of the same name;
+ * dist2, pred and flags may be NULL for none).  Every request is checked
+ * before any is queued: on an error nothing is queued, and the message names
+ * the request.  tickets receives count tickets.
+ */
+knn_status knn_server_submit_many(ghn_server* server, int32_t count, const int64_t* index_ids,
+                                  const float* const* queries, const int64_t* m, const int32_t* k,
+                                  const int32_t* mode, int32_t* const* ids, float* const* dist2,
+                                  void* const* pred, const int32_t* flags, int64_t* tickets);
 
 /*
  * knn_server_wait: wait up to timeout_us (negative: no limit) for a ticket.

@@ -9,8 +9,10 @@
 //               copy, one persistent batched query launch per dimension (each
 //               request is one entry of the launch; warps steal queries across
 //               all of them) and one device->host copy of the results;
-//   completer   waits for the slots in launch order, scatters each request's
-//               rows to the caller's buffers and completes its ticket;
+//   completers  (one per slot) each take the next launched slot, wait for
+//               it, scatter each request's rows to the caller's buffers and
+//               complete its ticket; the copies of consecutive batches run
+//               in parallel;
 //   builder     runs admitted builds (knn_build) on a stream of its own.
 // Up to max_inflight slots are on the GPU at once: requests that arrive while
 // batches run are queued and form the next batch as soon as a slot frees, and
@@ -166,11 +168,13 @@ struct ghn_server {
     int builds_running = 0;
     std::vector<Slot> slots;
     std::vector<int> free_slots;
-    std::deque<int> launched;  // slots on the GPU, in launch order
+    std::deque<int> launched;  // slots on the GPU not yet taken by a completer, in launch order
+    int inflight = 0;          // slots launched and not yet completed
     long long resident = 0, reserved = 0, buffers = 0;
     knn_server_stats_t st{};
     cudaStream_t build_stream = nullptr;
-    std::thread dispatcher, completer, builder;
+    std::thread dispatcher, builder;
+    std::vector<std::thread> completers;
 
     size_t cap_args() const { return align16((size_t)cfg.max_batch_requests * sizeof(QueryArgs)); }
     size_t cap_qoff() const { return align16(((size_t)cfg.max_batch_requests + kGroups) * 8); }
@@ -278,8 +282,12 @@ void ghn_server::dispatch_loop()
         st.max_batch_requests_seen = std::max(st.max_batch_requests_seen, (int64_t)sl.reqs.size());
         st.max_batch_queries_seen = std::max(st.max_batch_queries_seen, (int64_t)nq);
         lk.unlock();
+        const long long t0 = clock_ns();
         pack_and_launch(sl);
+        const long long t1 = clock_ns();
         lk.lock();
+        st.pack_ns += t1 - t0;
+        ++inflight;
         launched.push_back(si);
         cv_complete.notify_one();
     }
@@ -403,11 +411,14 @@ void ghn_server::complete_loop()
             continue;
         }
         const int si = launched.front();
+        launched.pop_front();
         lk.unlock();
         Slot& sl = slots[si];
+        const long long t0 = clock_ns();
         int batch_status = sl.launch_status;
         if (batch_status == KNN_OK && cudaEventSynchronize(sl.event) != cudaSuccess)
             batch_status = KNN_ECUDA;
+        const long long t1 = clock_ns();
         if (batch_status != KNN_OK) {
             // whatever was queued before the failure finishes before the
             // slot's buffers are reused
@@ -434,7 +445,9 @@ void ghn_server::complete_loop()
         }
         const long long now = clock_ns();
         lk.lock();
-        launched.pop_front();
+        st.wait_ns += t1 - t0;
+        st.scatter_ns += now - t1;
+        --inflight;
         for (size_t i = 0; i < sl.reqs.size(); ++i) {
             const TicketP& t = sl.reqs[i];
             complete(t, status[i], now);
@@ -632,7 +645,8 @@ knn_status knn_server_create(const knn_server_config* cfg_in, ghn_server** out)
     s->st.buffer_bytes = s->buffers;
     s->st.budget_bytes = c.memory_budget;
     s->dispatcher = std::thread([s] { s->dispatch_loop(); });
-    s->completer = std::thread([s] { s->complete_loop(); });
+    for (int i = 0; i < c.max_inflight; ++i)
+        s->completers.emplace_back([s] { s->complete_loop(); });
     s->builder = std::thread([s] { s->build_loop(); });
     cudaSetDevice(prev);
     *out = s;
@@ -708,32 +722,33 @@ knn_status knn_server_drop(ghn_server* s, int64_t index_id, int64_t* ticket)
     return KNN_OK;
 }
 
-knn_status knn_server_submit(ghn_server* s, int64_t index_id, const float* queries, int64_t m,
-                             int32_t k, int32_t mode, int32_t* ids, float* dist2, void* pred,
-                             int32_t flags, int64_t* ticket)
+}  // extern "C"
+
+namespace {
+
+// Checks of a query request that need no lock; the request's ticket on success.
+knn_status make_request(ghn_server* s, int64_t index_id, const float* queries, int64_t m,
+                        int32_t k, int32_t mode, int32_t* ids, float* dist2, void* pred,
+                        int32_t flags, const char* who, TicketP& out)
 {
-    if (!s || !ticket) {
-        ghn::set_error("knn_server_submit: NULL argument");
-        return KNN_EINVAL;
-    }
     if (flags & ~KNN_QUERY_EXACT) {
-        ghn::set_error("knn_server_submit: flags may only hold KNN_QUERY_EXACT");
+        set_errf("%s: flags may only hold KNN_QUERY_EXACT", who);
         return KNN_EINVAL;
     }
     if (m < 0 || k < 1 || k > ghn::kMaxK || mode < -1 || mode > 2) {
-        ghn::set_error("knn_server_submit: m must be >= 0, k in [1, 64], mode in {-1, 0, 1, 2}");
+        set_errf("%s: m must be >= 0, k in [1, 64], mode in {-1, 0, 1, 2}", who);
         return KNN_EINVAL;
     }
     if (m > 0 && (!queries || !ids || (mode >= 0 && !pred))) {
-        ghn::set_error("knn_server_submit: queries, ids (and pred for a prediction) are required");
+        set_errf("%s: queries, ids (and pred for a prediction) are required", who);
         return KNN_EINVAL;
     }
     if (m > 0 && (on_device(queries) || on_device(ids) || on_device(dist2) || on_device(pred))) {
-        ghn::set_error("knn_server_submit: queries and outputs must be host memory");
+        set_errf("%s: queries and outputs must be host memory", who);
         return KNN_EINVAL;
     }
     if (m > s->cfg.max_batch_queries || m * (int64_t)k > s->cfg.max_batch_outputs) {
-        set_errf("knn_server_submit: %lld queries x k = %d exceed one batch", (long long)m, k);
+        set_errf("%s: %lld queries x k = %d exceed one batch", who, (long long)m, k);
         return KNN_EINVAL;
     }
     auto t = std::make_shared<Ticket>();
@@ -747,34 +762,100 @@ knn_status knn_server_submit(ghn_server* s, int64_t index_id, const float* queri
     t->dist2 = dist2;
     t->pred = mode >= 0 ? pred : nullptr;
     t->exact = (flags & KNN_QUERY_EXACT) ? 1 : 0;
-    t->t_submit = clock_ns();
-    std::lock_guard<std::mutex> lk(s->mu);
-    auto it = s->indexes.find(index_id);
+    out = std::move(t);
+    return KNN_OK;
+}
+
+// The checks against the server's indexes (under mu).
+knn_status check_index(ghn_server* s, const Ticket& t, const char* who)
+{
+    auto it = s->indexes.find(t.index_id);
     if (it == s->indexes.end() || it->second.dropping) {
-        set_errf("knn_server_submit: unknown or dropped index %lld", (long long)index_id);
+        set_errf("%s: unknown or dropped index %lld", who, (long long)t.index_id);
         return KNN_EINVAL;
     }
-    IndexEntry& e = it->second;
-    if (mode >= 0 && !e.has_labels) {
-        ghn::set_error("knn_server_submit: a prediction needs an index built with labels");
+    if (t.mode >= 0 && !it->second.has_labels) {
+        set_errf("%s: a prediction needs an index built with labels", who);
         return KNN_EINVAL;
     }
+    return KNN_OK;
+}
+
+// Register a checked request and queue it (under mu).
+int64_t enqueue(ghn_server* s, const TicketP& t, long long now)
+{
+    IndexEntry& e = s->indexes[t->index_id];
     t->d = e.d;
+    t->t_submit = now;
     t->id = s->next_ticket++;
     s->tickets[t->id] = t;
-    *ticket = t->id;
-    if (m == 0) {
-        t->t_dispatch = t->t_submit;
-        s->complete(t, KNN_OK, t->t_submit);
-        return KNN_OK;
+    if (t->m == 0) {
+        t->t_dispatch = now;
+        s->complete(t, KNN_OK, now);
+        return t->id;
     }
     ++e.queued;
     if (e.ready) {
         s->queue.push_back(t);
-        s->cv_dispatch.notify_one();
     } else {
         e.parked.push_back(t);
     }
+    return t->id;
+}
+
+}  // namespace
+
+extern "C" {
+
+knn_status knn_server_submit(ghn_server* s, int64_t index_id, const float* queries, int64_t m,
+                             int32_t k, int32_t mode, int32_t* ids, float* dist2, void* pred,
+                             int32_t flags, int64_t* ticket)
+{
+    if (!s || !ticket) {
+        ghn::set_error("knn_server_submit: NULL argument");
+        return KNN_EINVAL;
+    }
+    TicketP t;
+    knn_status st = make_request(s, index_id, queries, m, k, mode, ids, dist2, pred, flags,
+                                 "knn_server_submit", t);
+    if (st != KNN_OK) return st;
+    const long long now = clock_ns();
+    std::lock_guard<std::mutex> lk(s->mu);
+    if ((st = check_index(s, *t, "knn_server_submit")) != KNN_OK) return st;
+    *ticket = enqueue(s, t, now);
+    s->cv_dispatch.notify_one();
+    return KNN_OK;
+}
+
+knn_status knn_server_submit_many(ghn_server* s, int32_t count, const int64_t* index_ids,
+                                  const float* const* queries, const int64_t* m, const int32_t* k,
+                                  const int32_t* mode, int32_t* const* ids, float* const* dist2,
+                                  void* const* pred, const int32_t* flags, int64_t* tickets)
+{
+    if (!s || count < 0 || (count > 0 && (!index_ids || !queries || !m || !k || !mode || !ids ||
+                                          !tickets))) {
+        ghn::set_error("knn_server_submit_many: NULL argument or negative count");
+        return KNN_EINVAL;
+    }
+    std::vector<TicketP> ts((size_t)count);
+    for (int32_t i = 0; i < count; ++i) {
+        char who[64];
+        snprintf(who, sizeof who, "knn_server_submit_many: request %d", i);
+        knn_status st = make_request(s, index_ids[i], queries[i], m[i], k[i], mode[i], ids[i],
+                                     dist2 ? dist2[i] : nullptr, pred ? pred[i] : nullptr,
+                                     flags ? flags[i] : 0, who, ts[(size_t)i]);
+        if (st != KNN_OK) return st;
+    }
+    const long long now = clock_ns();
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (int32_t i = 0; i < count; ++i) {
+        char who[64];
+        snprintf(who, sizeof who, "knn_server_submit_many: request %d", i);
+        knn_status st = check_index(s, *ts[(size_t)i], who);
+        if (st != KNN_OK) return st;  // nothing queued yet
+    }
+    for (int32_t i = 0; i < count; ++i) tickets[i] = enqueue(s, ts[(size_t)i], now);
+    s->cv_dispatch.notify_one();
     return KNN_OK;
 }
 
@@ -852,7 +933,7 @@ knn_status knn_server_stats(ghn_server* s, knn_server_stats_t* out)
     for (auto& kv : s->indexes) queued += (long long)kv.second.parked.size();
     v.queued_requests = queued;
     v.waiting_builds = (int64_t)s->builds_waiting.size();
-    v.inflight_batches = (int64_t)s->launched.size();
+    v.inflight_batches = (int64_t)s->inflight;
     *out = v;
     return KNN_OK;
 }
@@ -873,7 +954,7 @@ void knn_server_destroy(ghn_server* s)
         s->builds_waiting.clear();
         // finish everything admitted
         s->cv_done.wait(lk, [&] {
-            return s->queue.empty() && s->launched.empty() && s->builds_admitted.empty() &&
+            return s->queue.empty() && s->inflight == 0 && s->builds_admitted.empty() &&
                    s->builds_running == 0;
         });
         s->stop = true;
@@ -882,7 +963,7 @@ void knn_server_destroy(ghn_server* s)
         s->cv_build.notify_all();
     }
     s->dispatcher.join();
-    s->completer.join();
+    for (auto& t : s->completers) t.join();
     s->builder.join();
     int prev = 0;
     cudaGetDevice(&prev);

@@ -46,6 +46,7 @@ EXPORTED = ["knn_batch_build", "knn_batch_info", "knn_batch_query", "knn_batch_p
             "knn_timing_enable", "knn_timing_read", "knn_kernel_launches", "knn_free",
             "knn_last_error", "knn_abi_version",
             "knn_server_create", "knn_server_build", "knn_server_drop", "knn_server_submit",
+            "knn_server_submit_many",
             "knn_server_wait", "knn_server_test", "knn_server_stats", "knn_server_clock_ns",
             "knn_server_build_bytes", "knn_server_index", "knn_server_destroy"]
 
@@ -69,7 +70,7 @@ class knn_server_stats_t(ctypes.Structure):
         "batches", "requests_done", "queries_done", "builds_done", "drops_done", "indexes",
         "resident_bytes", "reserved_bytes", "buffer_bytes", "budget_bytes", "queued_requests",
         "waiting_builds", "inflight_batches", "max_batch_requests_seen",
-        "max_batch_queries_seen")]
+        "max_batch_queries_seen", "pack_ns", "wait_ns", "scatter_ns")]
 
 
 def library(path: str | None = None) -> ctypes.CDLL:
@@ -143,6 +144,10 @@ def library(path: str | None = None) -> ctypes.CDLL:
         lib.knn_server_drop.restype = i32
         lib.knn_server_submit.argtypes = [vp, i64, vp, i64, i32, i32, vp, vp, vp, i32, pi64]
         lib.knn_server_submit.restype = i32
+        lib.knn_server_submit_many.argtypes = [vp, i32, pi64, pp, pi64, ctypes.POINTER(i32),
+                                               ctypes.POINTER(i32), pp, pp, pp,
+                                               ctypes.POINTER(i32), pi64]
+        lib.knn_server_submit_many.restype = i32
         lib.knn_server_wait.argtypes = [vp, i64, i64, ctypes.POINTER(knn_ticket_info)]
         lib.knn_server_wait.restype = i32
         lib.knn_server_test.argtypes = [vp, i64, ctypes.POINTER(i32),
@@ -578,6 +583,46 @@ class Server:
         with self._klock:
             self._keep[t.value] = (q, ids, d2, pred)
         return t.value, ids, d2, pred
+
+    def submit_many(self, requests, want_dist2: bool = True):
+        """Queue many requests in one call: requests is a list of
+        (index_id, queries, k, mode[, flags]); returns [(ticket, ids, dist2, pred)]."""
+        n = len(requests)
+        c = ctypes
+        iid = (c.c_int64 * n)()
+        qp = (c.c_void_p * n)()
+        mm = (c.c_int64 * n)()
+        kk = (c.c_int32 * n)()
+        md = (c.c_int32 * n)()
+        ip = (c.c_void_p * n)()
+        dp = (c.c_void_p * n)()
+        pp_ = (c.c_void_p * n)()
+        fl = (c.c_int32 * n)()
+        tk = (c.c_int64 * n)()
+        out, keep = [], []
+        for i, r in enumerate(requests):
+            index_id, queries, k, mode = r[:4]
+            q = np.ascontiguousarray(queries, np.float32)
+            m = int(q.shape[0])
+            ids = np.empty((m, k), np.int32)
+            d2 = np.empty((m, k), np.float32) if want_dist2 else None
+            pred = None
+            if mode >= 0:
+                pred = np.empty(m, np.int32 if mode == KNN_VOTE else np.float32)
+            iid[i], qp[i], mm[i], kk[i], md[i] = index_id, q.ctypes.data, m, k, mode
+            ip[i] = ids.ctypes.data
+            dp[i] = d2.ctypes.data if d2 is not None else None
+            pp_[i] = pred.ctypes.data if pred is not None else None
+            fl[i] = r[4] if len(r) > 4 else 0
+            out.append([None, ids, d2, pred])
+            keep.append(q)
+        _check(library().knn_server_submit_many(self._h, n, iid, qp, mm, kk, md, ip, dp, pp_, fl,
+                                                tk))
+        with self._klock:
+            for i in range(n):
+                out[i][0] = tk[i]
+                self._keep[tk[i]] = (keep[i], out[i][1], out[i][2], out[i][3])
+        return [tuple(o) for o in out]
 
     def wait(self, ticket: int, timeout_us: int = -1):
         """Outcome of a ticket (knn_ticket_info), or None if the timeout ran out."""

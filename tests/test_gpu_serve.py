@@ -257,3 +257,20 @@ def test_device_buffers_are_rejected(server_with_indexes):
     rc = knn.library().knn_server_submit(srv._h, ids_of[0], q.data_ptr(), 4, 3, -1,
                                          ids.data_ptr(), None, None, 0, knn.ctypes.byref(t))
     assert rc == knn.KNN_EINVAL
+
+
+def test_submit_many_equals_single_submissions_and_is_all_or_nothing(server_with_indexes):
+    srv, ids_of, data = server_with_indexes
+    reqs = _requests(30, seed=8)
+    many = srv.submit_many([(ids_of[i], q, k, mode) for (i, q, k, mode) in reqs])
+    single, _ = _serve(srv, ids_of, reqs, together=False)
+    for (t, ids, d2, pred), ref in zip(many, single):
+        assert srv.wait(t).status == knn.KNN_OK
+        _same((ids, d2, pred), ref)
+    before = srv.stats().requests_done
+    bad = [(ids_of[0], np.zeros((3, 2), np.float32), 5, knn.KNN_VOTE),
+           (ids_of[0], np.zeros((3, 2), np.float32), 99, knn.KNN_VOTE)]  # k > 64
+    with pytest.raises(knn.KnnError) as e:
+        srv.submit_many(bad)
+    assert "request 1" in str(e.value)
+    assert srv.stats().requests_done == before and srv.stats().queued_requests == 0
