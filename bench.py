@@ -121,9 +121,106 @@ def oracle_step(w: wl.Workload, sample: int, offset: int = 0):
     return scaled, {"build_s": t_build, "query_s": t_query, "sample_queries": s, "cores": cores}
 
 
+def oracle_problems(problems, widths, budget_s: float = 15.0):
+    """Time the oracle on whole problems (build + every query, threads over
+    queries), in a fixed sample order, until about budget_s has been spent.
+
+    Returns (queries per second over the problems done, details)."""
+    import oracle
+
+    cores = host_cores()
+    order = np.random.default_rng(0).permutation(len(problems))
+    spent, qdone, done = 0.0, 0, 0
+    for i in order:
+        p_ = problems[i]
+        t0 = time.perf_counter()
+        g = oracle.Grid(p_.points, p_.labels, widths[i])
+        chunks = [c for c in np.array_split(np.arange(p_.m), cores * 4) if len(c)]
+        with cf.ThreadPoolExecutor(max_workers=cores) as ex:  # ctypes releases the GIL
+            list(ex.map(lambda c: g.query(p_.queries[c], p_.k, p_.mode), chunks))
+        g.close()
+        spent += time.perf_counter() - t0
+        qdone += p_.m
+        done += 1
+        if spent >= budget_s:
+            break
+    return qdone / spent, {"problems": done, "of": len(problems), "queries": qdone,
+                           "seconds": spent, "cores": cores}
+
+
+def oracle_requests(specs, widths, qev, dev, budget_s: float = 15.0, n_cap: int = 2_000_000):
+    """The oracle answering served requests, in arrival order, on the indexes of
+    at most n_cap points (threads over a request's queries).  Its grids are
+    built outside the timing, as the server's indexes are resident."""
+    import oracle
+
+    cores = host_cores()
+    grids, spent, qn, nreq = {}, 0.0, 0, 0
+    for e in qev:
+        if specs[e.index].n > n_cap:
+            continue
+        if e.index not in grids:
+            pts, lab = wl.serving_points(specs[e.index], dev)
+            grids[e.index] = oracle.Grid(pts.cpu().numpy(), lab.cpu().numpy(), widths[e.index])
+        g = grids[e.index]
+        chunks = [c for c in np.array_split(np.arange(e.queries.shape[0]), cores) if len(c)]
+        t0 = time.perf_counter()
+        with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+            list(ex.map(lambda c: g.query(e.queries[c], e.k, e.mode), chunks))
+        spent += time.perf_counter() - t0
+        qn += e.queries.shape[0]
+        nreq += 1
+        if spent >= budget_s:
+            break
+    for g in grids.values():
+        g.close()
+    return {"value": qn / max(spent, 1e-9), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"{nreq} requests ({qn} queries) in arrival order on the indexes of at most "
+                       f"{n_cap} points ({len(grids)} of {len(specs)}), {spent:.1f} s of query time, "
+                       f"grids built untimed")}
+
+
+def run_reference_batched(args):
+    """The oracle on the batched workload (widths: the autotuner's starting
+    guess, as tuning needs the GPU)."""
+    from paper_2004_02290_gb300 import autotune
+
+    ps = wl.gen_batched(args.batch_count, seed=3)
+    widths = [autotune.start_width(p_.points, p_.k) for p_ in ps]
+    vals = []
+    det = None
+    for i in range(args.warmup + args.steps):
+        v, det = oracle_problems(ps, widths, budget_s=10.0)
+        if i >= args.warmup:
+            vals.append(v)
+    value = float(np.mean(vals))
+    total_q = sum(p_.m for p_ in ps)
+    sample = (f"{det['problems']} of {det['of']} problems per step, whole (build + all queries, "
+              f"{det['cores']} threads); widths: the autotuner's starting guess")
+    print(json.dumps({
+        "impl": "reference", "metric": "queries/sec, batched vs plain grid-KNN (build + query per step)",
+        "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_q / value * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batched", "problems": len(ps), "queries": int(total_q)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": det["cores"], "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
+        return
+    if args.config == "batched":
+        run_reference_batched(args)
+        return
+    if args.config == "serving":
+        print(json.dumps({"impl": "reference", "unavailable":
+                          "the serving workload's resident indexes (300 M points) are beyond "
+                          "the oracle's few-minute budget; its per-request time is reported "
+                          "as cpu_baseline in the served line"}), flush=True)
         return
     w = wl.make(args.config)
     times = []
@@ -557,6 +654,12 @@ def run_batched(args):
     plan.free()
     batch.free()
     total_q = sum(p_.m for p_ in ps)
+    cpu = None
+    if not args.no_cpu_baseline:
+        v, det = oracle_problems(ps, widths)
+        cpu = {"value": v, "unit": UNIT, "cores": det["cores"], "kind": "oracle",
+               "sample": (f"{det['problems']} of {det['of']} problems, whole (build + all "
+                          f"queries, {det['cores']} threads, {det['seconds']:.1f} s), same widths")}
     b_step = float(np.mean(b_ms))
     p_step = float(np.mean(p_ms))
     print(json.dumps({
@@ -573,7 +676,7 @@ def run_batched(args):
         "speedup_vs_plain": p_step / b_step,
         "query_only_ms": {"direct": float(np.mean(q_ms)), "graph_replay": float(np.mean(g_ms))},
         "identical_to_plain": bool(identical), "graph_identical": bool(graph_identical),
-        "gpu_launches_batched": int(lb), "clocks": clocks,
+        "gpu_launches_batched": int(lb), "clocks": clocks, "cpu_baseline": cpu,
     }), flush=True)
 
 
@@ -625,7 +728,7 @@ def run_serving(args):
 
     # ---- resident indexes: autotuned width (k = 16), built through the server ----
     t_setup = time.perf_counter()
-    ids, tune_s = [], 0.0
+    ids, tune_s, widths = [], 0.0, []
     for ix in specs:
         pts, lab = wl.serving_points(ix, dev)
         qs = torch.from_numpy(wl.serving_queries(ix, 4096, np.random.default_rng(ix.seed))).to(dev)
@@ -637,6 +740,7 @@ def run_serving(args):
         if info.status != knn.KNN_OK:
             raise RuntimeError(f"build of a resident index failed: status {info.status}")
         ids.append(iid)
+        widths.append(w)
         del pts, lab, qs
     # points of the interleaved builds, drawn before the clock starts
     extra = []
@@ -781,6 +885,9 @@ def run_serving(args):
 
     cap_served = q_total / served_s
     cap_plain = q_total / plain_s
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = oracle_requests(specs, widths, qev, dev)
     h2d = sum(e.queries.nbytes for e in qev) / len(qev)
     d2h = sum(o[0].nbytes + o[1].nbytes + o[2].nbytes for o in outs_s) / len(qev)
     print(json.dumps({
@@ -823,7 +930,7 @@ def run_serving(args):
         "identical_to_plain": bool(identical),
         "e2e": {"value": cap_served, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": int(launches), "clocks": clocks,
+        "gpu_launches": int(launches), "clocks": clocks, "cpu_baseline": cpu,
     }), flush=True)
 
 
