@@ -274,3 +274,41 @@ def test_submit_many_equals_single_submissions_and_is_all_or_nothing(server_with
         srv.submit_many(bad)
     assert "request 1" in str(e.value)
     assert srv.stats().requests_done == before and srv.stats().queued_requests == 0
+
+
+_FAILED_BUILD = r"""
+import numpy as np
+from paper_2004_02290_gb300 import knn, workloads as wl
+srv = knn.Server(max_inflight=1, max_batch_queries=4096, max_batch_requests=16)
+x, lab, q = wl.uniform(3000, 20, 2, seed=1)
+a, ta = srv.build(x, lab, 0.05)           # its first allocation fails (injected)
+tq, ids, _, _ = srv.submit(a, q, 5, knn.KNN_VOTE)  # parked on the failing build
+ia, iq = srv.wait(ta), srv.wait(tq)
+b, tb = srv.build(x, lab, 0.05)           # the next build works
+ib = srv.wait(tb)
+t2, ids2, _, _ = srv.submit(b, q, 5, knn.KNN_VOTE)
+i2 = srv.wait(t2)
+try:
+    srv.submit(a, q, 5, knn.KNN_VOTE)
+    gone = False
+except knn.KnnError:
+    gone = True
+srv.close()
+print("STATUS", ia.status, iq.status, ib.status, i2.status, gone)
+"""
+
+
+def test_failed_build_fails_its_parked_queries_and_the_server_goes_on():
+    """A build whose allocation fails (host-side injector): its ticket reports
+    KNN_ENOMEM, the queries parked on it KNN_EINVAL, the index is gone, and the
+    next build and its queries succeed."""
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, GHN_FAIL_ALLOC_AT="1", PYTHONPATH=root)
+    r = subprocess.run([sys.executable, "-c", _FAILED_BUILD], cwd=root, env=env,
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-3000:]
+    assert f"STATUS {knn.KNN_ENOMEM} {knn.KNN_EINVAL} 0 0 True" in r.stdout, r.stdout
