@@ -719,25 +719,6 @@ __device__ __forceinline__ void write_outputs(const QueryArgs& a, long long qid,
 // The warp kernel: one warp per query
 // ---------------------------------------------------------------------------
 
-// Row position of flattened candidate t: the lane whose ranges hold it by
-// binary search over the lanes' inclusive ends.
-__device__ __forceinline__ unsigned int search_pos(const unsigned int* end, const unsigned int* beg,
-                                                   const unsigned int* sa, const unsigned int* la,
-                                                   const unsigned int* sb, unsigned int t)
-{
-    int lo_l = 0, hi_l = 31;
-#pragma unroll
-    for (int it = 0; it < 5; ++it) {
-        const int mid = (lo_l + hi_l) >> 1;
-        if (end[mid] > t)
-            hi_l = mid;
-        else
-            lo_l = mid + 1;
-    }
-    const unsigned int off = t - beg[lo_l];
-    const unsigned int ln = la[lo_l];
-    return off < ln ? sa[lo_l] + off : sb[lo_l] + (off - ln);
-}
 
 // Resident blocks per SM the warp kernel is compiled for.  The walk is bound by
 // memory latency, so more resident warps pay even when the register cap
@@ -756,6 +737,31 @@ struct WarpSmem {
     unsigned int la[32];   // first range: length
     unsigned int b[32];    // second range: start
 };
+
+// The lane whose ranges hold flattened candidate t (t < end[31]): binary
+// search over the lanes' inclusive ends.
+__device__ __forceinline__ unsigned int owner_of(const unsigned int* end, unsigned int t)
+{
+    int lo_l = 0, hi_l = 31;
+#pragma unroll
+    for (int it = 0; it < 5; ++it) {
+        const int mid = (lo_l + hi_l) >> 1;
+        if (end[mid] > t)
+            hi_l = mid;
+        else
+            lo_l = mid + 1;
+    }
+    return (unsigned int)lo_l;
+}
+
+// Row position of flattened candidate t, held by lane `own`'s ranges.
+__device__ __forceinline__ unsigned int pos_in(const WarpSmem& sm, unsigned int own,
+                                               unsigned int t)
+{
+    const unsigned int off = t - sm.beg[own];
+    const unsigned int ln = sm.la[own];
+    return off < ln ? sm.a[own] + off : sm.b[own] + (off - ln);
+}
 
 // One query by one warp.  Returns true when the query was deferred to the
 // cooperative kernel (nothing written); otherwise its outputs are written.
@@ -828,8 +834,13 @@ __device__ __forceinline__ bool walk_query(const QueryArgs& a, long long qid, Wa
                 constexpr int P = row_floats(D);
                 Row<P> nrow;
                 unsigned int nrid = 0u;
+                // own: the lane whose ranges hold this lane's next candidate,
+                // found by binary search for the first chunk and then moved
+                // forward (positions only grow, by 32 a chunk)
+                unsigned int own = 0u;
                 if (lane < total) {
-                    const unsigned int pos = search_pos(sm.end, sm.beg, sm.a, sm.la, sm.b, lane);
+                    own = owner_of(sm.end, lane);
+                    const unsigned int pos = pos_in(sm, own, lane);
                     nrow.load(a.rows, pos);
                     nrid = __ldg(a.rid + pos);
                 }
@@ -838,8 +849,9 @@ __device__ __forceinline__ bool walk_query(const QueryArgs& a, long long qid, Wa
                     const Row<P> row = nrow;
                     const unsigned int rid = nrid;
                     if (t + 32u < total) {
-                        const unsigned int pos =
-                            search_pos(sm.end, sm.beg, sm.a, sm.la, sm.b, t + 32u);
+                        const unsigned int tn = t + 32u;
+                        while (sm.end[own] <= tn) ++own;  // ends at 31 at the latest
+                        const unsigned int pos = pos_in(sm, own, tn);
                         nrow.load(a.rows, pos);
                         nrid = __ldg(a.rid + pos);
                     }
