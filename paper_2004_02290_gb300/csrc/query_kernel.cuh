@@ -197,6 +197,16 @@ __device__ __forceinline__ float axis_gap2(long long c0, long long c1, float u, 
     return gw * gw;
 }
 
+// The same bound for cells inside the box (32-bit coordinates: extents stay
+// below 2^31, so c1 + 1 fits), with single-word conversions.
+__device__ __forceinline__ float axis_gap2(int c0, int c1, float u, float w)
+{
+    const float lo = (float)c0, hi = (float)(c1 + 1);
+    const float g = fmaxf(0.0f, fmaxf(lo - u, u - hi) - axis_margin(fabsf(lo) + fabsf(hi), u));
+    const float gw = g * w;
+    return gw * gw;
+}
+
 // Bits [b0, b1] of the occupancy bitmap: first and last set bit (b1 + 1 if none).
 __device__ __forceinline__ void bitmap_span(const unsigned int* bm, unsigned long long b0,
                                             unsigned long long b1, unsigned long long& first,
@@ -487,7 +497,7 @@ __device__ __forceinline__ void row_ranges(const QueryArgs& a, unsigned long lon
         const long long dd = c > s.c0[j] ? c - s.c0[j] : s.c0[j] - c;
         ocheb = dd > ocheb ? dd : ocheb;
         base += (unsigned long long)c * a.g.stride[j];
-        og2 += axis_gap2(c, c, s.u[j], a.g.w[j]);
+        og2 += axis_gap2((int)c, (int)c, s.u[j], a.g.w[j]);
     }
     long long x0a, x1a, x0b, x1b;
     if (ocheb == L) {
@@ -528,10 +538,12 @@ __device__ __forceinline__ void row_ranges(const QueryArgs& a, unsigned long lon
         x1b = x1b < c1 ? x1b : c1;
     }
     if (x0a <= x1a &&
-        !(prune && (og2 + axis_gap2(x0a, x1a, s.u[dl], a.g.w[dl])) * (1.0f - 1e-5f) > kth_d))
+        !(prune && (og2 + axis_gap2((int)x0a, (int)x1a, s.u[dl], a.g.w[dl])) * (1.0f - 1e-5f) >
+                       kth_d))
         resolve_run<DENSE>(a, hmask, base, x0a, x1a, counting, sa, la, cells);
     if (x0b <= x1b &&
-        !(prune && (og2 + axis_gap2(x0b, x1b, s.u[dl], a.g.w[dl])) * (1.0f - 1e-5f) > kth_d))
+        !(prune && (og2 + axis_gap2((int)x0b, (int)x1b, s.u[dl], a.g.w[dl])) * (1.0f - 1e-5f) >
+                       kth_d))
         resolve_run<DENSE>(a, hmask, base, x0b, x1b, counting, sb, lb, cells);
     if (la == 0u) {
         sa = sb;
