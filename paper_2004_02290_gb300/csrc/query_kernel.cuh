@@ -215,14 +215,17 @@ __device__ __forceinline__ void bitmap_span(const unsigned int* bm, unsigned lon
     first = b1 + 1ull;
     last = b1 + 1ull;
     count = 0;
-    const unsigned long long w0 = b0 >> 5, w1 = b1 >> 5;
-    for (unsigned long long wi = w0; wi <= w1; ++wi) {
+    // a bitmap exists only for boxes of at most 2^33 cells: word indices fit
+    // 32 bits
+    const unsigned int w0 = (unsigned int)(b0 >> 5), w1 = (unsigned int)(b1 >> 5);
+    for (unsigned int wi = w0; wi <= w1; ++wi) {
         unsigned int word = __ldg(bm + wi);
-        if (wi == w0) word &= 0xffffffffu << (b0 & 31ull);
-        if (wi == w1) word &= 0xffffffffu >> (31ull - (b1 & 31ull));
+        if (wi == w0) word &= 0xffffffffu << ((unsigned int)b0 & 31u);
+        if (wi == w1) word &= 0xffffffffu >> (31u - ((unsigned int)b1 & 31u));
         if (word) {
-            if (first > b1) first = (wi << 5) + (unsigned long long)(__ffs(word) - 1);
-            last = (wi << 5) + (unsigned long long)(31 - __clz(word));
+            const unsigned long long at = (unsigned long long)wi << 5;
+            if (first > b1) first = at + (unsigned long long)(__ffs(word) - 1);
+            last = at + (unsigned long long)(31 - __clz(word));
             if (want_count) count += __popc(word);
         }
     }
