@@ -736,12 +736,13 @@ __device__ __forceinline__ void write_outputs(const QueryArgs& a, long long qid,
 
 
 // Resident blocks per SM the warp kernel is compiled for.  The walk is bound by
-// memory latency, so more resident warps pay even when the register cap
-// spills a little to L1 (measured on the d=3 and d=4 workloads; for d >= 5
-// four blocks fit without spills and more gave nothing).
+// memory latency and instruction issue, so more resident warps pay even when
+// the register cap spills a little to L1 (measured: 8 blocks on the d=3 and
+// d=4 workloads; 6 for d=5 and 6, 3% faster than 4 on the heaviest d=6
+// problems; 4 for the larger query state of d=7 and 8).
 template <int D, int NS>
 struct MinBlocks {
-    static constexpr int value = NS == 1 ? (D <= 4 ? 8 : 4) : 2;
+    static constexpr int value = NS == 1 ? (D <= 4 ? 8 : (D <= 6 ? 6 : 4)) : 2;
 };
 
 // Per-warp shared memory of the walk: the lanes' ranges of one row batch.
