@@ -217,3 +217,38 @@ def test_cooperative_kernel_exact_and_per_dimension_widths():
                        text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-3000:]
     assert "BAD 0" in r.stdout, r.stdout
+
+
+@pytest.mark.parametrize("table", [knn.KNN_TABLE_DENSE, knn.KNN_TABLE_HASH])
+@pytest.mark.parametrize("d,k,mode,rule", [
+    (1, 64, knn.KNN_MEDIAN, oracle.RULE_PAPER),
+    (5, 40, knn.KNN_MEAN, oracle.RULE_EXACT),
+    (7, 33, knn.KNN_VOTE, oracle.RULE_PAPER),
+    (8, 64, knn.KNN_MEDIAN, oracle.RULE_EXACT),
+])
+def test_wide_buffers_and_high_dimensions_per_dimension_widths(d, k, mode, rule, table):
+    """Two-slot buffers (k > 32), d = 1, 5, 7, 8, every head, both rules."""
+    x, lab, q = wl.uniform(3000, 120, d, seed=900 + d)
+    if mode != knn.KNN_VOTE:
+        lab = (np.round(wl.regression_targets(x, seed=d) * 8) / 8).astype(np.float32)
+    w = (np.float32(0.08 + 0.07 * d) * (1.0 + 0.2 * np.arange(d))).astype(np.float32)
+    q = np.concatenate([q, np.full((1, d), -0.25, np.float32)]).astype(np.float32)
+    idx = knn.knn_build_grid(_dev(x), _dev(lab), w, None, table)
+    flags = knn.KNN_QUERY_CHECKED | (knn.KNN_QUERY_EXACT if rule == oracle.RULE_EXACT else 0)
+    got = idx.query(_dev(q), k, mode, flags=flags)
+    _same(got, oracle.Grid(x, lab, w).query(q, k, mode, rule=rule))
+    idx.free()
+
+
+def test_measured_grid_one_dimension():
+    rng = np.random.default_rng(44)
+    x = np.round(rng.normal(0.5, 0.2, (4000, 1)) * 200).astype(np.float32) / np.float32(200)
+    lab = rng.integers(0, 3, size=4000).astype(np.int32)
+    q = rng.normal(0.5, 0.25, (300, 1)).astype(np.float32)
+    splits, widths = knn.knn_measure_cells(_dev(x))
+    e_splits, e_widths = oracle.measure_cells(x)
+    assert splits.tolist() == e_splits.tolist() and np.array_equal(widths, e_widths)
+    idx = knn.knn_build_grid(_dev(x), _dev(lab), widths, splits)
+    got = idx.query(_dev(q), 9, knn.KNN_VOTE, flags=knn.KNN_QUERY_CHECKED)
+    _same(got, oracle.Grid(x, lab, widths, splits=splits).query(q, 9, knn.KNN_VOTE))
+    idx.free()
