@@ -378,7 +378,8 @@ def _sampled_full(name, sample, flags):
     rng = np.random.default_rng(123)
     pick = np.sort(rng.choice(w.m, size=sample, replace=False))
     g = oracle.Grid(w.points, w.labels, w.w)
-    exp = g.query(w.queries[pick], w.k, w.mode)
+    rule = oracle.RULE_EXACT if flags & knn.KNN_QUERY_EXACT else oracle.RULE_PAPER
+    exp = g.query(w.queries[pick], w.k, w.mode, rule=rule)
     got = (ids.cpu().numpy()[pick], d2.cpu().numpy()[pick], pred.cpu().numpy()[pick])
     assert_same(got, exp, w.mode)
     # properties that hold for every row: sorted, distinct, in range
@@ -405,6 +406,14 @@ def test_full_skewed_reg_sampled():
     import bench
 
     _sampled_full("skewed_reg", 1500, bench.QUERY_FLAGS)
+
+
+def test_full_large_cls_sampled_certified_stop():
+    _sampled_full("large_cls", 1500, knn.KNN_QUERY_EXACT)
+
+
+def test_full_skewed_reg_sampled_certified_stop():
+    _sampled_full("skewed_reg", 800, knn.KNN_QUERY_EXACT)
 
 
 _FORCED_DEFERRAL = r"""
