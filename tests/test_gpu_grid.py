@@ -252,3 +252,17 @@ def test_measured_grid_one_dimension():
     got = idx.query(_dev(q), 9, knn.KNN_VOTE, flags=knn.KNN_QUERY_CHECKED)
     _same(got, oracle.Grid(x, lab, widths, splits=splits).query(q, 9, knn.KNN_VOTE))
     idx.free()
+
+
+def test_exact_flag_with_locality_order_and_host_buffers():
+    """KNN_QUERY_EXACT combined with KNN_QUERY_SORTED, and with host buffers."""
+    x, lab, q = wl.uniform(8000, 500, 3, seed=77)
+    q = np.concatenate([q, np.full((2, 3), 1.5, np.float32)]).astype(np.float32)
+    exp = oracle.Grid(x, lab, 0.05).query(q, 12, knn.KNN_VOTE, rule=oracle.RULE_EXACT)
+    idx = knn.knn_build(_dev(x), _dev(lab), 0.05)
+    got = idx.query(_dev(q), 12, knn.KNN_VOTE,
+                    flags=knn.KNN_QUERY_EXACT | knn.KNN_QUERY_SORTED | knn.KNN_QUERY_CHECKED)
+    _same(got, exp)
+    got_host = idx.query(q, 12, knn.KNN_VOTE, flags=knn.KNN_QUERY_EXACT | knn.KNN_QUERY_CHECKED)
+    _same(got_host, exp)
+    idx.free()
