@@ -236,7 +236,8 @@ knn_status knn_batch_info(const ghn_batch* batch, int32_t i, knn_index_info_t* i
 
 /*
  * knn_batch_query: query every index of the batch (host arrays of count
- * entries; every data pointer is device memory; m[i] may be 0).  Outputs of
+ * entries; every data pointer is device memory; m[i] may be 0; the sum of
+ * the m[i] must be below 2^32).  Outputs of
  * index i as knn_query's.  flags: KNN_QUERY_CHECKED, KNN_QUERY_EXACT.
  */
 knn_status knn_batch_query(const ghn_batch* batch, const float* const* queries, const int64_t* m,

@@ -774,6 +774,13 @@ knn_status plan_layout(const ghn_batch* b, const float* const* queries, const in
             return KNN_EINVAL;
         }
     }
+    // the deferred-query list holds 32-bit positions within a group
+    unsigned long long all = 0ull;
+    for (int i = 0; i < b->count; ++i) all += (unsigned long long)m[i];
+    if (all >= (1ull << 32)) {
+        set_error("knn_batch_query: more than 2^32 - 1 queries in one call");
+        return KNN_EINVAL;
+    }
     // one group per (dimension, buffer width, table kind): each launches a
     // kernel specialised for all three
     for (int key = 0; key < 4 * (kMaxD + 1); ++key) {
