@@ -172,37 +172,40 @@ __global__ void cell_keys_kernel(const float* __restrict__ pts, long long n, Gri
 }
 
 // ---------------------------------------------------------------------------
-// Stable LSD radix sort, 8-bit digits, 2048-element tiles (256 threads x 8).
-// Per pass: a digit histogram per tile, an exclusive scan of the digit-major
-// histogram table, and a scatter that ranks each tile stably in shared memory
-// and writes it out in digit runs.
+// Stable LSD radix sort, 8- or 9-bit digits (256 or 512 buckets), 2048-element
+// tiles (256 threads x 8).  Per pass: a digit histogram per tile, an exclusive
+// scan of the digit-major histogram table, and a scatter that ranks each tile
+// stably in shared memory and writes it out in digit runs.
 // ---------------------------------------------------------------------------
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;
-constexpr int kRadix = 256;
+constexpr int kRadixMax = 512;
 
+template <int R>
 __global__ void __launch_bounds__(kSortThreads)
     radix_hist_kernel(const unsigned long long* __restrict__ keys, long long n, int shift,
                       unsigned int* __restrict__ hist, unsigned int nb)
 {
-    __shared__ unsigned int cnt[kRadix];
+    __shared__ unsigned int cnt[R];
     const int t = threadIdx.x;
-    cnt[t] = 0u;
+    for (int e = t; e < R; e += kSortThreads) cnt[e] = 0u;
     __syncthreads();
     const long long base = (long long)blockIdx.x * kSortTile;
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         const long long i = base + r * kSortThreads + t;
         const bool valid = i < n;
-        const unsigned dg = valid ? (unsigned)((keys[i] >> shift) & 0xffu) : 0x100u + (t & 31);
+        const unsigned dg =
+            valid ? (unsigned)((keys[i] >> shift) & (unsigned long long)(R - 1)) : R + (t & 31);
         const unsigned peers = __match_any_sync(FULL, dg);
         if (valid && (peers & lanemask_lt()) == 0u) atomicAdd(&cnt[dg], __popc(peers));
     }
     __syncthreads();
-    hist[(size_t)t * nb + blockIdx.x] = cnt[t];
+    for (int e = t; e < R; e += kSortThreads) hist[(size_t)e * nb + blockIdx.x] = cnt[e];
 }
 
+template <int R>
 __global__ void __launch_bounds__(kSortThreads)
     radix_scatter_kernel(const unsigned long long* __restrict__ kin,
                          const unsigned int* __restrict__ vin,
@@ -211,16 +214,18 @@ __global__ void __launch_bounds__(kSortThreads)
                          unsigned int nb)
 {
     constexpr int W = kSortThreads / 32;
-    __shared__ unsigned int wcnt[W][kRadix];
-    __shared__ unsigned int dig_off[kRadix];
-    __shared__ unsigned int gbase[kRadix];
+    constexpr int DPT = R / kSortThreads;  // digits per thread in the digit scan
+    constexpr unsigned long long MASK = (unsigned long long)(R - 1);
+    __shared__ unsigned int wcnt[W][R];
+    __shared__ unsigned int dig_off[R];
+    __shared__ unsigned int gbase[R];
     __shared__ unsigned int wsum[W];
     __shared__ unsigned long long skey[kSortTile];
     __shared__ unsigned int sval[kSortTile];
 
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    for (int e = t; e < W * kRadix; e += kSortThreads) (&wcnt[0][0])[e] = 0u;
-    gbase[t] = scanned[(size_t)t * nb + blockIdx.x];
+    for (int e = t; e < W * R; e += kSortThreads) (&wcnt[0][0])[e] = 0u;
+    for (int e = t; e < R; e += kSortThreads) gbase[e] = scanned[(size_t)e * nb + blockIdx.x];
     __syncthreads();
 
     const long long tile = (long long)blockIdx.x * kSortTile;
@@ -234,7 +239,7 @@ __global__ void __launch_bounds__(kSortThreads)
         const bool valid = local < count;
         k[r] = valid ? kin[tile + local] : 0ull;
         v[r] = valid ? vin[tile + local] : 0u;
-        const unsigned d = valid ? (unsigned)((k[r] >> shift) & 0xffu) : 0x100u + lane;
+        const unsigned d = valid ? (unsigned)((k[r] >> shift) & MASK) : R + lane;
         const unsigned peers = __match_any_sync(FULL, d);
         const unsigned before = __popc(peers & lanemask_lt());
         unsigned int b = 0u;
@@ -246,16 +251,25 @@ __global__ void __launch_bounds__(kSortThreads)
         dg[r] = d;
     }
     __syncthreads();
-    // per digit: exclusive prefix over warps, and the tile's total
-    unsigned int run = 0u;
+    // per digit: exclusive prefix over warps, and the tile's total; thread t
+    // owns the consecutive digits t*DPT .. t*DPT + DPT - 1
+    unsigned int run[DPT];
+    unsigned int mine = 0u;
 #pragma unroll
-    for (int w = 0; w < W; ++w) {
-        const unsigned int c = wcnt[w][t];
-        wcnt[w][t] = run;
-        run += c;
+    for (int q = 0; q < DPT; ++q) {
+        const int e = t * DPT + q;
+        unsigned int acc = 0u;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            const unsigned int c = wcnt[w][e];
+            wcnt[w][e] = acc;
+            acc += c;
+        }
+        run[q] = acc;
+        mine += acc;
     }
-    // exclusive scan of the 256 digit totals (one per thread)
-    unsigned int x = run;
+    // exclusive scan of the digit totals over the threads
+    unsigned int x = mine;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const unsigned int y = __shfl_up_sync(FULL, x, o);
@@ -265,11 +279,16 @@ __global__ void __launch_bounds__(kSortThreads)
     __syncthreads();
     unsigned int wpre = 0u;
     for (int w = 0; w < warp; ++w) wpre += wsum[w];
-    dig_off[t] = wpre + x - run;
+    unsigned int off = wpre + x - mine;
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+        dig_off[t * DPT + q] = off;
+        off += run[q];
+    }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
-        if (dg[r] < 0x100u) {
+        if (dg[r] < (unsigned)R) {
             const unsigned int p = dig_off[dg[r]] + wcnt[warp][dg[r]] + rank[r];
             skey[p] = k[r];
             sval[p] = v[r];
@@ -278,7 +297,7 @@ __global__ void __launch_bounds__(kSortThreads)
     __syncthreads();
     for (int i = t; i < count; i += kSortThreads) {
         const unsigned long long key = skey[i];
-        const unsigned d = (unsigned)((key >> shift) & 0xffu);
+        const unsigned d = (unsigned)((key >> shift) & MASK);
         const unsigned int g = gbase[d] + (unsigned int)i - dig_off[d];
         kout[g] = key;
         vout[g] = sval[i];
@@ -616,7 +635,7 @@ cudaError_t scan_exclusive(const unsigned int* in, unsigned int* out, long long 
 size_t radix_temp_bytes(long long n)
 {
     const long long nb = (n + kSortTile - 1) / kSortTile;
-    const long long entries = (nb > 0 ? nb : 1) * kRadix;
+    const long long entries = (nb > 0 ? nb : 1) * kRadixMax;
     size_t hist = (size_t)entries * sizeof(unsigned int);
     hist = (hist + 255) & ~(size_t)255;
     return hist + scan_temp_bytes(entries);
@@ -628,19 +647,36 @@ cudaError_t radix_sort_pairs(unsigned long long* keys_a, unsigned int* vals_a,
                              unsigned int** result_vals, cudaStream_t s)
 {
     const long long nb = (n + kSortTile - 1) / kSortTile;
-    const long long entries = nb * kRadix;
     unsigned int* hist = static_cast<unsigned int*>(temp);
-    size_t hist_bytes = ((size_t)entries * sizeof(unsigned int) + 255) & ~(size_t)255;
+    const size_t hist_bytes =
+        ((size_t)(nb * kRadixMax) * sizeof(unsigned int) + 255) & ~(size_t)255;
     void* scan_tmp = static_cast<char*>(temp) + hist_bytes;
     unsigned long long *kin = keys_a, *kout = keys_b;
     unsigned int *vin = vals_a, *vout = vals_b;
-    for (int shift = 0; shift < bits && n > 1; shift += 8) {
-        radix_hist_kernel<<<(unsigned)nb, kSortThreads, 0, s>>>(kin, n, shift, hist,
-                                                                 (unsigned)nb);
+    // passes: 8-bit digits, except that when 9-bit digits need fewer passes
+    // (bits mod 8 small), the top `wide` passes take 9 bits
+    const int p8 = (bits + 7) / 8, p9 = (bits + 8) / 9;
+    const int passes = p9 < p8 ? p9 : p8;
+    const int wide = p9 < p8 ? bits - 8 * passes : 0;
+    int shift = 0;
+    for (int pass = 0; pass < passes && n > 1; ++pass) {
+        const bool w9 = pass >= passes - wide;
+        const long long entries = nb * (w9 ? 512 : 256);
+        if (w9)
+            radix_hist_kernel<512><<<(unsigned)nb, kSortThreads, 0, s>>>(kin, n, shift, hist,
+                                                                          (unsigned)nb);
+        else
+            radix_hist_kernel<256><<<(unsigned)nb, kSortThreads, 0, s>>>(kin, n, shift, hist,
+                                                                          (unsigned)nb);
         cudaError_t e = scan_exclusive(hist, hist, entries, scan_tmp, s);
         if (e != cudaSuccess) return e;
-        radix_scatter_kernel<<<(unsigned)nb, kSortThreads, 0, s>>>(kin, vin, kout, vout, n, shift,
-                                                                    hist, (unsigned)nb);
+        if (w9)
+            radix_scatter_kernel<512><<<(unsigned)nb, kSortThreads, 0, s>>>(
+                kin, vin, kout, vout, n, shift, hist, (unsigned)nb);
+        else
+            radix_scatter_kernel<256><<<(unsigned)nb, kSortThreads, 0, s>>>(
+                kin, vin, kout, vout, n, shift, hist, (unsigned)nb);
+        shift += w9 ? 9 : 8;
         count_launches(2);
         unsigned long long* tk = kin;
         kin = kout;
