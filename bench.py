@@ -41,7 +41,8 @@ METRIC = "queries/sec (index build + batched query per step)"
 QUERY_FLAGS = 0
 UNIT = "queries/s"
 L2_FLUSH_BYTES = 512 << 20
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "query_kernel_large_cls_ncu.md")
+# ncu summary of the query kernel on a workload: profiles/query_kernel_<workload>_ncu.md
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "query_kernel_{}_ncu.md")
 
 
 def parse_args(argv=None):
@@ -335,9 +336,10 @@ def query_kernel_sha() -> str:
 def profiled_traffic(workload: str):
     """DRAM bytes per launch of the query kernel from the committed ncu summary,
     if it was taken on the current kernel source and this workload."""
-    if not os.path.exists(PROFILE_SUMMARY):
+    path = PROFILE_SUMMARY.format(workload)
+    if not os.path.exists(path):
         return None
-    with open(PROFILE_SUMMARY) as f:
+    with open(path) as f:
         text = f.read()
     sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
     wk = re.search(r"workload:\s*(\S+)", text)

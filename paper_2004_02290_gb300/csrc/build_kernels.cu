@@ -34,6 +34,8 @@ __device__ __forceinline__ unsigned lanemask_lt()
 // thread always sees the same dimension (threadIdx.x % d) of the row-major
 // array, and the loads of a warp are contiguous.
 // ---------------------------------------------------------------------------
+constexpr int kBoxUnroll = 8;
+
 __global__ void box_partial_kernel(const float* __restrict__ pts, long long total, int d,
                                    float* __restrict__ partial)
 {
@@ -46,7 +48,20 @@ __global__ void box_partial_kernel(const float* __restrict__ pts, long long tota
     float lo = INFINITY, hi = -INFINITY;
     bool bad = false;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long e = (long long)blockIdx.x * blockDim.x + t; e < total; e += stride) {
+    long long e = (long long)blockIdx.x * blockDim.x + t;
+    // kBoxUnroll independent loads in flight per thread, all of one dimension
+    for (; e + (kBoxUnroll - 1) * stride < total; e += kBoxUnroll * stride) {
+        float v[kBoxUnroll];
+#pragma unroll
+        for (int r = 0; r < kBoxUnroll; ++r) v[r] = __ldg(pts + e + r * stride);
+#pragma unroll
+        for (int r = 0; r < kBoxUnroll; ++r) {
+            bad |= !isfinite(v[r]);
+            lo = fminf(lo, v[r]);
+            hi = fmaxf(hi, v[r]);
+        }
+    }
+    for (; e < total; e += stride) {
         const float v = __ldg(pts + e);
         bad |= !isfinite(v);
         lo = fminf(lo, v);
@@ -151,9 +166,9 @@ __global__ void __launch_bounds__(kBoxFinalThreads)
 // clamped to split_j - 1 on a grid with splits, then the linear id
 // sum_j c_j * stride_j; the value is the point's index.
 // ---------------------------------------------------------------------------
-template <int D>
+template <int D, class K>
 __global__ void cell_keys_kernel(const float* __restrict__ pts, long long n, GridConst g,
-                                 unsigned long long* __restrict__ keys,
+                                 K* __restrict__ keys,
                                  unsigned int* __restrict__ vals)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -166,14 +181,15 @@ __global__ void cell_keys_kernel(const float* __restrict__ pts, long long n, Gri
             if (g.split[j] > 0 && c > g.split[j] - 1) c = g.split[j] - 1;
             key += (unsigned long long)c * g.stride[j];
         }
-        keys[i] = key;
+        keys[i] = (K)key;  // 32-bit K only when every id of the box fits
         vals[i] = (unsigned int)i;
     }
 }
 
 // ---------------------------------------------------------------------------
 // Stable LSD radix sort, 8- or 9-bit digits (256 or 512 buckets), 2048-element
-// tiles (256 threads x 8).  Per pass: a digit histogram per tile, an exclusive
+// tiles (256 threads x 8), of 64-bit keys or, when every key fits, 32-bit ones
+// (20 bytes a pass per element instead of 32).  Per pass: a digit histogram per tile, an exclusive
 // scan of the digit-major histogram table, and a scatter that ranks each tile
 // stably in shared memory and writes it out in digit runs.
 // ---------------------------------------------------------------------------
@@ -182,9 +198,9 @@ constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kRadixMax = 512;
 
-template <int R>
+template <class K, int R>
 __global__ void __launch_bounds__(kSortThreads)
-    radix_hist_kernel(const unsigned long long* __restrict__ keys, long long n, int shift,
+    radix_hist_kernel(const K* __restrict__ keys, long long n, int shift,
                       unsigned int* __restrict__ hist, unsigned int nb)
 {
     __shared__ unsigned int cnt[R];
@@ -197,7 +213,7 @@ __global__ void __launch_bounds__(kSortThreads)
         const long long i = base + r * kSortThreads + t;
         const bool valid = i < n;
         const unsigned dg =
-            valid ? (unsigned)((keys[i] >> shift) & (unsigned long long)(R - 1)) : R + (t & 31);
+            valid ? (unsigned)((keys[i] >> shift) & (K)(R - 1)) : R + (t & 31);
         const unsigned peers = __match_any_sync(FULL, dg);
         if (valid && (peers & lanemask_lt()) == 0u) atomicAdd(&cnt[dg], __popc(peers));
     }
@@ -205,22 +221,21 @@ __global__ void __launch_bounds__(kSortThreads)
     for (int e = t; e < R; e += kSortThreads) hist[(size_t)e * nb + blockIdx.x] = cnt[e];
 }
 
-template <int R>
+template <class K, int R>
 __global__ void __launch_bounds__(kSortThreads)
-    radix_scatter_kernel(const unsigned long long* __restrict__ kin,
-                         const unsigned int* __restrict__ vin,
-                         unsigned long long* __restrict__ kout, unsigned int* __restrict__ vout,
+    radix_scatter_kernel(const K* __restrict__ kin, const unsigned int* __restrict__ vin,
+                         K* __restrict__ kout, unsigned int* __restrict__ vout,
                          long long n, int shift, const unsigned int* __restrict__ scanned,
                          unsigned int nb)
 {
     constexpr int W = kSortThreads / 32;
     constexpr int DPT = R / kSortThreads;  // digits per thread in the digit scan
-    constexpr unsigned long long MASK = (unsigned long long)(R - 1);
+    constexpr K MASK = (K)(R - 1);
     __shared__ unsigned int wcnt[W][R];
     __shared__ unsigned int dig_off[R];
     __shared__ unsigned int gbase[R];
     __shared__ unsigned int wsum[W];
-    __shared__ unsigned long long skey[kSortTile];
+    __shared__ K skey[kSortTile];
     __shared__ unsigned int sval[kSortTile];
 
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -230,14 +245,14 @@ __global__ void __launch_bounds__(kSortThreads)
 
     const long long tile = (long long)blockIdx.x * kSortTile;
     const long long count = n - tile < kSortTile ? n - tile : kSortTile;
-    unsigned long long k[kSortItems];
+    K k[kSortItems];
     unsigned int v[kSortItems], rank[kSortItems], dg[kSortItems];
     // warp `warp` ranks elements [warp*256, warp*256+256) of the tile, in order
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         const int local = warp * (32 * kSortItems) + r * 32 + lane;
         const bool valid = local < count;
-        k[r] = valid ? kin[tile + local] : 0ull;
+        k[r] = valid ? kin[tile + local] : (K)0;
         v[r] = valid ? vin[tile + local] : 0u;
         const unsigned d = valid ? (unsigned)((k[r] >> shift) & MASK) : R + lane;
         const unsigned peers = __match_any_sync(FULL, d);
@@ -296,7 +311,7 @@ __global__ void __launch_bounds__(kSortThreads)
     }
     __syncthreads();
     for (int i = t; i < count; i += kSortThreads) {
-        const unsigned long long key = skey[i];
+        const K key = skey[i];
         const unsigned d = (unsigned)((key >> shift) & MASK);
         const unsigned int g = gbase[d] + (unsigned int)i - dig_off[d];
         kout[g] = key;
@@ -398,7 +413,8 @@ __global__ void __launch_bounds__(kScanThreads)
 // Cells: a head flag where the sorted id changes; the exclusive scan of the
 // flags numbers the cells.  Each head writes its cell's id and first row.
 // ---------------------------------------------------------------------------
-__global__ void head_flags_kernel(const unsigned long long* __restrict__ keys, long long n,
+template <class K>
+__global__ void head_flags_kernel(const K* __restrict__ keys, long long n,
                                   unsigned int* __restrict__ flags)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -406,7 +422,8 @@ __global__ void head_flags_kernel(const unsigned long long* __restrict__ keys, l
         flags[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
 }
 
-__global__ void cells_write_kernel(const unsigned long long* __restrict__ keys, long long n,
+template <class K>
+__global__ void cells_write_kernel(const K* __restrict__ keys, long long n,
                                    const unsigned int* __restrict__ flags,
                                    const unsigned int* __restrict__ cid,
                                    unsigned long long* __restrict__ cell_key,
@@ -415,7 +432,7 @@ __global__ void cells_write_kernel(const unsigned long long* __restrict__ keys, 
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         if (flags[i]) {
-            cell_key[cid[i]] = keys[i];
+            cell_key[cid[i]] = (unsigned long long)keys[i];
             cell_start[cid[i]] = (unsigned int)i;
         }
         if (i == n - 1) {
@@ -521,9 +538,9 @@ __global__ void gather_kernel(const float* __restrict__ pts, long long n,
 }
 
 // Cell id of each query clamped into the box (for the locality order only).
-template <int D>
+template <int D, class K>
 __global__ void query_keys_kernel(const float* __restrict__ q, long long m, GridConst g,
-                                  unsigned long long* __restrict__ keys,
+                                  K* __restrict__ keys,
                                   unsigned int* __restrict__ vals)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -537,7 +554,7 @@ __global__ void query_keys_kernel(const float* __restrict__ q, long long m, Grid
             if (c > g.cmax[j]) c = g.cmax[j];
             key += (unsigned long long)c * g.stride[j];
         }
-        keys[i] = key;
+        keys[i] = (K)key;  // 32-bit K only when every id of the box fits
         vals[i] = (unsigned int)i;
     }
 }
@@ -560,7 +577,7 @@ int box_partial_blocks(long long n)
 {
     long long b = (n + 255) / 256;
     if (b < 1) b = 1;
-    if (b > 152 * 4) b = 152 * 4;
+    if (b > 152 * 8) b = 152 * 8;
     return (int)b;
 }
 
@@ -575,42 +592,72 @@ cudaError_t launch_box(const float* pts, long long n, int d, const Widths& w, fl
     return cudaGetLastError();
 }
 
-cudaError_t launch_cell_keys(const float* pts, long long n, const GridConst& g,
-                             unsigned long long* keys, unsigned int* vals, cudaStream_t s)
+namespace {
+template <class K>
+cudaError_t launch_cell_keys_t(const float* pts, long long n, const GridConst& g, K* keys,
+                                unsigned int* vals, cudaStream_t s)
 {
     const int b = grid_for(n, 256);
     count_launches(1);
     switch (g.d) {
-    case 1: cell_keys_kernel<1><<<b, 256, 0, s>>>(pts, n, g, keys, vals); break;
-    case 2: cell_keys_kernel<2><<<b, 256, 0, s>>>(pts, n, g, keys, vals); break;
-    case 3: cell_keys_kernel<3><<<b, 256, 0, s>>>(pts, n, g, keys, vals); break;
-    case 4: cell_keys_kernel<4><<<b, 256, 0, s>>>(pts, n, g, keys, vals); break;
-    case 5: cell_keys_kernel<5><<<b, 256, 0, s>>>(pts, n, g, keys, vals); break;
-    case 6: cell_keys_kernel<6><<<b, 256, 0, s>>>(pts, n, g, keys, vals); break;
-    case 7: cell_keys_kernel<7><<<b, 256, 0, s>>>(pts, n, g, keys, vals); break;
-    case 8: cell_keys_kernel<8><<<b, 256, 0, s>>>(pts, n, g, keys, vals); break;
+    case 1: cell_keys_kernel<1, K><<<b, 256, 0, s>>>(pts, n, g, keys, vals); break;
+    case 2: cell_keys_kernel<2, K><<<b, 256, 0, s>>>(pts, n, g, keys, vals); break;
+    case 3: cell_keys_kernel<3, K><<<b, 256, 0, s>>>(pts, n, g, keys, vals); break;
+    case 4: cell_keys_kernel<4, K><<<b, 256, 0, s>>>(pts, n, g, keys, vals); break;
+    case 5: cell_keys_kernel<5, K><<<b, 256, 0, s>>>(pts, n, g, keys, vals); break;
+    case 6: cell_keys_kernel<6, K><<<b, 256, 0, s>>>(pts, n, g, keys, vals); break;
+    case 7: cell_keys_kernel<7, K><<<b, 256, 0, s>>>(pts, n, g, keys, vals); break;
+    case 8: cell_keys_kernel<8, K><<<b, 256, 0, s>>>(pts, n, g, keys, vals); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
+}  // namespace
 
-cudaError_t launch_query_keys(const float* q, long long m, const GridConst& g,
-                              unsigned long long* keys, unsigned int* vals, cudaStream_t s)
+cudaError_t launch_cell_keys(const float* pts, long long n, const GridConst& g,
+                             unsigned long long* keys, unsigned int* vals, cudaStream_t s)
+{
+    return launch_cell_keys_t(pts, n, g, keys, vals, s);
+}
+
+cudaError_t launch_cell_keys(const float* pts, long long n, const GridConst& g, unsigned int* keys,
+                             unsigned int* vals, cudaStream_t s)
+{
+    return launch_cell_keys_t(pts, n, g, keys, vals, s);
+}
+
+namespace {
+template <class K>
+cudaError_t launch_query_keys_t(const float* q, long long m, const GridConst& g, K* keys,
+                                 unsigned int* vals, cudaStream_t s)
 {
     const int b = grid_for(m, 256);
     count_launches(1);
     switch (g.d) {
-    case 1: query_keys_kernel<1><<<b, 256, 0, s>>>(q, m, g, keys, vals); break;
-    case 2: query_keys_kernel<2><<<b, 256, 0, s>>>(q, m, g, keys, vals); break;
-    case 3: query_keys_kernel<3><<<b, 256, 0, s>>>(q, m, g, keys, vals); break;
-    case 4: query_keys_kernel<4><<<b, 256, 0, s>>>(q, m, g, keys, vals); break;
-    case 5: query_keys_kernel<5><<<b, 256, 0, s>>>(q, m, g, keys, vals); break;
-    case 6: query_keys_kernel<6><<<b, 256, 0, s>>>(q, m, g, keys, vals); break;
-    case 7: query_keys_kernel<7><<<b, 256, 0, s>>>(q, m, g, keys, vals); break;
-    case 8: query_keys_kernel<8><<<b, 256, 0, s>>>(q, m, g, keys, vals); break;
+    case 1: query_keys_kernel<1, K><<<b, 256, 0, s>>>(q, m, g, keys, vals); break;
+    case 2: query_keys_kernel<2, K><<<b, 256, 0, s>>>(q, m, g, keys, vals); break;
+    case 3: query_keys_kernel<3, K><<<b, 256, 0, s>>>(q, m, g, keys, vals); break;
+    case 4: query_keys_kernel<4, K><<<b, 256, 0, s>>>(q, m, g, keys, vals); break;
+    case 5: query_keys_kernel<5, K><<<b, 256, 0, s>>>(q, m, g, keys, vals); break;
+    case 6: query_keys_kernel<6, K><<<b, 256, 0, s>>>(q, m, g, keys, vals); break;
+    case 7: query_keys_kernel<7, K><<<b, 256, 0, s>>>(q, m, g, keys, vals); break;
+    case 8: query_keys_kernel<8, K><<<b, 256, 0, s>>>(q, m, g, keys, vals); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_query_keys(const float* q, long long m, const GridConst& g,
+                              unsigned long long* keys, unsigned int* vals, cudaStream_t s)
+{
+    return launch_query_keys_t(q, m, g, keys, vals, s);
+}
+
+cudaError_t launch_query_keys(const float* q, long long m, const GridConst& g, unsigned int* keys,
+                              unsigned int* vals, cudaStream_t s)
+{
+    return launch_query_keys_t(q, m, g, keys, vals, s);
 }
 
 size_t scan_temp_bytes(long long n)
@@ -641,17 +688,18 @@ size_t radix_temp_bytes(long long n)
     return hist + scan_temp_bytes(entries);
 }
 
-cudaError_t radix_sort_pairs(unsigned long long* keys_a, unsigned int* vals_a,
-                             unsigned long long* keys_b, unsigned int* vals_b, long long n,
-                             int bits, void* temp, unsigned long long** result_keys,
-                             unsigned int** result_vals, cudaStream_t s)
+namespace {
+template <class K>
+cudaError_t radix_sort_pairs_t(K* keys_a, unsigned int* vals_a, K* keys_b, unsigned int* vals_b,
+                               long long n, int bits, void* temp, K** result_keys,
+                               unsigned int** result_vals, cudaStream_t s)
 {
     const long long nb = (n + kSortTile - 1) / kSortTile;
     unsigned int* hist = static_cast<unsigned int*>(temp);
     const size_t hist_bytes =
         ((size_t)(nb * kRadixMax) * sizeof(unsigned int) + 255) & ~(size_t)255;
     void* scan_tmp = static_cast<char*>(temp) + hist_bytes;
-    unsigned long long *kin = keys_a, *kout = keys_b;
+    K *kin = keys_a, *kout = keys_b;
     unsigned int *vin = vals_a, *vout = vals_b;
     // passes: 8-bit digits, except that when 9-bit digits need fewer passes
     // (bits mod 8 small), the top `wide` passes take 9 bits
@@ -663,22 +711,22 @@ cudaError_t radix_sort_pairs(unsigned long long* keys_a, unsigned int* vals_a,
         const bool w9 = pass >= passes - wide;
         const long long entries = nb * (w9 ? 512 : 256);
         if (w9)
-            radix_hist_kernel<512><<<(unsigned)nb, kSortThreads, 0, s>>>(kin, n, shift, hist,
+            radix_hist_kernel<K, 512><<<(unsigned)nb, kSortThreads, 0, s>>>(kin, n, shift, hist,
                                                                           (unsigned)nb);
         else
-            radix_hist_kernel<256><<<(unsigned)nb, kSortThreads, 0, s>>>(kin, n, shift, hist,
+            radix_hist_kernel<K, 256><<<(unsigned)nb, kSortThreads, 0, s>>>(kin, n, shift, hist,
                                                                           (unsigned)nb);
         cudaError_t e = scan_exclusive(hist, hist, entries, scan_tmp, s);
         if (e != cudaSuccess) return e;
         if (w9)
-            radix_scatter_kernel<512><<<(unsigned)nb, kSortThreads, 0, s>>>(
+            radix_scatter_kernel<K, 512><<<(unsigned)nb, kSortThreads, 0, s>>>(
                 kin, vin, kout, vout, n, shift, hist, (unsigned)nb);
         else
-            radix_scatter_kernel<256><<<(unsigned)nb, kSortThreads, 0, s>>>(
+            radix_scatter_kernel<K, 256><<<(unsigned)nb, kSortThreads, 0, s>>>(
                 kin, vin, kout, vout, n, shift, hist, (unsigned)nb);
         shift += w9 ? 9 : 8;
         count_launches(2);
-        unsigned long long* tk = kin;
+        K* tk = kin;
         kin = kout;
         kout = tk;
         unsigned int* tv = vin;
@@ -689,20 +737,58 @@ cudaError_t radix_sort_pairs(unsigned long long* keys_a, unsigned int* vals_a,
     *result_vals = vin;
     return cudaGetLastError();
 }
+}  // namespace
+
+cudaError_t radix_sort_pairs(unsigned long long* keys_a, unsigned int* vals_a,
+                             unsigned long long* keys_b, unsigned int* vals_b, long long n,
+                             int bits, void* temp, unsigned long long** result_keys,
+                             unsigned int** result_vals, cudaStream_t s)
+{
+    return radix_sort_pairs_t(keys_a, vals_a, keys_b, vals_b, n, bits, temp, result_keys,
+                              result_vals, s);
+}
+
+cudaError_t radix_sort_pairs(unsigned int* keys_a, unsigned int* vals_a, unsigned int* keys_b,
+                             unsigned int* vals_b, long long n, int bits, void* temp,
+                             unsigned int** result_keys, unsigned int** result_vals,
+                             cudaStream_t s)
+{
+    return radix_sort_pairs_t(keys_a, vals_a, keys_b, vals_b, n, bits, temp, result_keys,
+                              result_vals, s);
+}
+
+namespace {
+template <class K>
+cudaError_t launch_cells_t(const K* sorted_keys, long long n, unsigned int* flags_tmp,
+                           unsigned int* cid_tmp, void* scan_tmp, unsigned long long* cell_key,
+                           unsigned int* cell_start, GridDev* gdev, cudaStream_t s)
+{
+    const int b = grid_for(n, 256);
+    head_flags_kernel<K><<<b, 256, 0, s>>>(sorted_keys, n, flags_tmp);
+    cudaError_t e = scan_exclusive(flags_tmp, cid_tmp, n, scan_tmp, s);
+    if (e != cudaSuccess) return e;
+    cells_write_kernel<K><<<b, 256, 0, s>>>(sorted_keys, n, flags_tmp, cid_tmp, cell_key,
+                                            cell_start, gdev);
+    count_launches(2);
+    return cudaGetLastError();
+}
+}  // namespace
 
 cudaError_t launch_cells(const unsigned long long* sorted_keys, long long n,
                          unsigned int* flags_tmp, unsigned int* cid_tmp, void* scan_tmp,
                          unsigned long long* cell_key, unsigned int* cell_start, GridDev* gdev,
                          cudaStream_t s)
 {
-    const int b = grid_for(n, 256);
-    head_flags_kernel<<<b, 256, 0, s>>>(sorted_keys, n, flags_tmp);
-    cudaError_t e = scan_exclusive(flags_tmp, cid_tmp, n, scan_tmp, s);
-    if (e != cudaSuccess) return e;
-    cells_write_kernel<<<b, 256, 0, s>>>(sorted_keys, n, flags_tmp, cid_tmp, cell_key, cell_start,
-                                         gdev);
-    count_launches(2);
-    return cudaGetLastError();
+    return launch_cells_t(sorted_keys, n, flags_tmp, cid_tmp, scan_tmp, cell_key, cell_start,
+                          gdev, s);
+}
+
+cudaError_t launch_cells(const unsigned int* sorted_keys, long long n, unsigned int* flags_tmp,
+                         unsigned int* cid_tmp, void* scan_tmp, unsigned long long* cell_key,
+                         unsigned int* cell_start, GridDev* gdev, cudaStream_t s)
+{
+    return launch_cells_t(sorted_keys, n, flags_tmp, cid_tmp, scan_tmp, cell_key, cell_start,
+                          gdev, s);
 }
 
 cudaError_t launch_dense_table(const unsigned long long* cell_key, const unsigned int* cell_start,

@@ -385,15 +385,18 @@ knn_status build_impl(const float* points_user, const void* labels_user, long lo
         x->table = table;
 
         // ---- Eq. 1 keys, stable sort by cell, cell offsets, table, row gather ----
-        unsigned long long *ka = nullptr, *kb = nullptr;
+        // 32-bit keys when every cell id of the box fits (space <= 2^32)
+        const bool narrow = bits <= 32;
+        char *ka = nullptr, *kb = nullptr;
         unsigned int *va = nullptr, *vb = nullptr;
         void* rtmp = nullptr;
         unsigned int *flags = nullptr, *cid = nullptr;
         void* stmp = nullptr;
         unsigned long long* cell_key = nullptr;
         unsigned int* cell_start = nullptr;
-        st = tmp.alloc(&ka, (size_t)n, "keys");
-        if (st == KNN_OK) st = tmp.alloc(&kb, (size_t)n, "keys");
+        const size_t key_bytes = narrow ? sizeof(unsigned int) : sizeof(unsigned long long);
+        st = tmp.alloc(&ka, (size_t)n * key_bytes, "keys");
+        if (st == KNN_OK) st = tmp.alloc(&kb, (size_t)n * key_bytes, "keys");
         if (st == KNN_OK) st = dalloc(&va, (size_t)n, s, "row ids");
         if (st == KNN_OK) st = dalloc(&vb, (size_t)n, s, "row ids");
         if (st == KNN_OK) st = tmp.alloc(reinterpret_cast<char**>(&rtmp), radix_temp_bytes(n), "sort temp");
@@ -402,11 +405,24 @@ knn_status build_impl(const float* points_user, const void* labels_user, long lo
             dfree(vb, s);
             return fail(st);
         }
-        unsigned long long* sk = nullptr;
+        void* sk = nullptr;
         unsigned int* sv = nullptr;
-        e = launch_cell_keys(pts, n, g, ka, va, s);
-        g_timer.mark("keys", s);
-        if (e == cudaSuccess) e = radix_sort_pairs(ka, va, kb, vb, n, bits, rtmp, &sk, &sv, s);
+        if (narrow) {
+            auto k32a = reinterpret_cast<unsigned int*>(ka), k32b = reinterpret_cast<unsigned int*>(kb);
+            unsigned int* sk32 = nullptr;
+            e = launch_cell_keys(pts, n, g, k32a, va, s);
+            g_timer.mark("keys", s);
+            if (e == cudaSuccess) e = radix_sort_pairs(k32a, va, k32b, vb, n, bits, rtmp, &sk32, &sv, s);
+            sk = sk32;
+        } else {
+            auto k64a = reinterpret_cast<unsigned long long*>(ka);
+            auto k64b = reinterpret_cast<unsigned long long*>(kb);
+            unsigned long long* sk64 = nullptr;
+            e = launch_cell_keys(pts, n, g, k64a, va, s);
+            g_timer.mark("keys", s);
+            if (e == cudaSuccess) e = radix_sort_pairs(k64a, va, k64b, vb, n, bits, rtmp, &sk64, &sv, s);
+            sk = sk64;
+        }
         g_timer.mark("sort", s);
         if (e != cudaSuccess) {
             dfree(va, s);
@@ -432,7 +448,10 @@ knn_status build_impl(const float* points_user, const void* labels_user, long lo
         if (st != KNN_OK) {
             return fail(st);
         }
-        e = launch_cells(sk, n, flags, cid, stmp, cell_key, cell_start, x->gdev, s);
+        e = narrow ? launch_cells(static_cast<const unsigned int*>(sk), n, flags, cid, stmp, cell_key,
+                                  cell_start, x->gdev, s)
+                   : launch_cells(static_cast<const unsigned long long*>(sk), n, flags, cid, stmp,
+                                  cell_key, cell_start, x->gdev, s);
         if (e != cudaSuccess) {
             return fail(cuda_fail(e, "cells"));
         }
@@ -527,20 +546,33 @@ knn_status query_impl(const ghn_index* x, const float* queries_user, long long m
 
         const unsigned int* order = nullptr;
         if ((flags & KNN_QUERY_SORTED) && m > 1 && x->key_bits > 0) {
-            unsigned long long *ka = nullptr, *kb = nullptr;
+            // 32-bit keys when every cell id of the box fits
+            const bool narrow = x->key_bits <= 32;
+            const size_t key_bytes = narrow ? sizeof(unsigned int) : sizeof(unsigned long long);
+            char *ka = nullptr, *kb = nullptr;
             unsigned int *va = nullptr, *vb = nullptr;
             char* rtmp = nullptr;
-            st = tmp.alloc(&ka, (size_t)m, "query keys");
-            if (st == KNN_OK) st = tmp.alloc(&kb, (size_t)m, "query keys");
+            st = tmp.alloc(&ka, (size_t)m * key_bytes, "query keys");
+            if (st == KNN_OK) st = tmp.alloc(&kb, (size_t)m * key_bytes, "query keys");
             if (st == KNN_OK) st = tmp.alloc(&va, (size_t)m, "query order");
             if (st == KNN_OK) st = tmp.alloc(&vb, (size_t)m, "query order");
             if (st == KNN_OK) st = tmp.alloc(&rtmp, radix_temp_bytes(m), "sort temp");
             if (st != KNN_OK) return st;
-            unsigned long long* sk;
             unsigned int* sv;
-            GHN_CHECK(launch_query_keys(q, m, x->g, ka, va, s), "query keys");
-            GHN_CHECK(radix_sort_pairs(ka, va, kb, vb, m, x->key_bits, rtmp, &sk, &sv, s),
-                      "query order");
+            if (narrow) {
+                auto k32a = reinterpret_cast<unsigned int*>(ka), k32b = reinterpret_cast<unsigned int*>(kb);
+                unsigned int* sk;
+                GHN_CHECK(launch_query_keys(q, m, x->g, k32a, va, s), "query keys");
+                GHN_CHECK(radix_sort_pairs(k32a, va, k32b, vb, m, x->key_bits, rtmp, &sk, &sv, s),
+                          "query order");
+            } else {
+                auto k64a = reinterpret_cast<unsigned long long*>(ka);
+                auto k64b = reinterpret_cast<unsigned long long*>(kb);
+                unsigned long long* sk;
+                GHN_CHECK(launch_query_keys(q, m, x->g, k64a, va, s), "query keys");
+                GHN_CHECK(radix_sort_pairs(k64a, va, k64b, vb, m, x->key_bits, rtmp, &sk, &sv, s),
+                          "query order");
+            }
             order = sv;
         }
 

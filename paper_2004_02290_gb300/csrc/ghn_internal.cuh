@@ -77,6 +77,8 @@ int box_partial_blocks(long long n);
 
 cudaError_t launch_cell_keys(const float* pts, long long n, const GridConst& g,
                              unsigned long long* keys, unsigned int* vals, cudaStream_t s);
+cudaError_t launch_cell_keys(const float* pts, long long n, const GridConst& g, unsigned int* keys,
+                             unsigned int* vals, cudaStream_t s);  // every id < 2^32
 
 // LSD radix sort of (key, value) by the low `bits` bits of the key; stable.
 // Returns in *result_keys / *result_vals the buffers that hold the sorted data.
@@ -85,6 +87,10 @@ cudaError_t radix_sort_pairs(unsigned long long* keys_a, unsigned int* vals_a,
                              unsigned long long* keys_b, unsigned int* vals_b, long long n,
                              int bits, void* temp, unsigned long long** result_keys,
                              unsigned int** result_vals, cudaStream_t s);
+cudaError_t radix_sort_pairs(unsigned int* keys_a, unsigned int* vals_a, unsigned int* keys_b,
+                             unsigned int* vals_b, long long n, int bits, void* temp,
+                             unsigned int** result_keys, unsigned int** result_vals,
+                             cudaStream_t s);
 
 // Exclusive prefix sum of n uint32 values (out may alias in).
 size_t scan_temp_bytes(long long n);
@@ -95,6 +101,9 @@ cudaError_t launch_cells(const unsigned long long* sorted_keys, long long n,
                          unsigned int* flags_tmp, unsigned int* cid_tmp, void* scan_tmp,
                          unsigned long long* cell_key, unsigned int* cell_start, GridDev* gdev,
                          cudaStream_t s);
+cudaError_t launch_cells(const unsigned int* sorted_keys, long long n, unsigned int* flags_tmp,
+                         unsigned int* cid_tmp, void* scan_tmp, unsigned long long* cell_key,
+                         unsigned int* cell_start, GridDev* gdev, cudaStream_t s);
 
 // Dense table: dstart[id] = first row of cell id, for every id of the box, and
 // dstart[ncell_space] = n.  scan_tmp: scan_temp_bytes(ncell_space + 1).
@@ -210,5 +219,7 @@ cudaError_t launch_query_d78(const QueryArgs& a, int sms, cudaStream_t s);
 // Query keys for the locality order (cell id of each query, clamped into the box).
 cudaError_t launch_query_keys(const float* q, long long m, const GridConst& g,
                               unsigned long long* keys, unsigned int* vals, cudaStream_t s);
+cudaError_t launch_query_keys(const float* q, long long m, const GridConst& g, unsigned int* keys,
+                              unsigned int* vals, cudaStream_t s);  // every id < 2^32
 
 }  // namespace ghn

@@ -71,15 +71,32 @@ def test_method_bytes_counts_each_term():
 
 
 def test_profiled_traffic_ignores_stale_summaries(tmp_path, monkeypatch):
-    p = tmp_path / "s.md"
+    p = tmp_path / "q_large_cls.md"
     p.write_text("workload: large_cls\nkernel_source_sha256_16: 0000\n"
                  "dram_bytes_per_launch: 123\n")
-    monkeypatch.setattr(bench, "PROFILE_SUMMARY", str(p))
+    monkeypatch.setattr(bench, "PROFILE_SUMMARY", str(tmp_path / "q_{}.md"))
     assert bench.profiled_traffic("large_cls") is None
     p.write_text(f"workload: large_cls\nkernel_source_sha256_16: {bench.query_kernel_sha()}\n"
                  "dram_bytes_per_launch: 123\n")
     assert bench.profiled_traffic("large_cls") == 123.0
-    assert bench.profiled_traffic("skewed_reg") is None
+    assert bench.profiled_traffic("skewed_reg") is None  # no summary for it
+    # a summary filed under one workload's name but taken on another
+    (tmp_path / "q_tiny.md").write_text(
+        f"workload: large_cls\nkernel_source_sha256_16: {bench.query_kernel_sha()}\n"
+        "dram_bytes_per_launch: 123\n")
+    assert bench.profiled_traffic("tiny") is None
+
+
+def test_committed_summaries_match_their_names():
+    import glob
+    import re
+    for path in glob.glob(os.path.join(ROOT, "profiles", "query_kernel_*_ncu.md")):
+        text = open(path).read()
+        wk = re.search(r"workload:\s*(\S+)", text)
+        assert wk, path
+        name = os.path.basename(path)[len("query_kernel_"):-len("_ncu.md")]
+        if name in ("large_cls", "skewed_reg", "tiny"):
+            assert wk.group(1) == name, path
 
 
 def test_reference_arm_prints_one_line():

@@ -215,6 +215,24 @@ def test_far_query_fine_grid():
         assert_same(got, oracle_run(x, lab, q, 1e-6, k, knn.KNN_VOTE), knn.KNN_VOTE)
 
 
+@pytest.mark.parametrize("flags", [0, knn.KNN_QUERY_SORTED])
+@pytest.mark.parametrize("hi0,space", [(65535.5, 1 << 32), (65536.5, 65537 << 16)])
+def test_cell_id_width_boundary(hi0, space, flags):
+    """A box of exactly 2^32 cells (ids fill 32 bits: the build and the
+    locality order sort 32-bit keys) and one just above it (64-bit keys)."""
+    rng = np.random.default_rng(31)
+    centres = np.array([[100.0, 100.0], [30000.0, 50000.0], [65000.0, 65000.0]])
+    x = np.concatenate([c + 3.0 * rng.standard_normal((2000, 2)) for c in centres])
+    x = np.clip(x, 0.0, 65535.5)
+    x = np.concatenate([x, [[0.0, 0.0], [hi0, 65535.5]]]).astype(np.float32)
+    lab = rng.integers(0, 4, len(x)).astype(np.int32)
+    q = np.concatenate([c + 4.0 * rng.standard_normal((100, 2)) for c in centres]).astype(np.float32)
+    got, info = gpu_run(x, lab, q, 1.0, 5, knn.KNN_VOTE, flags=flags)
+    assert int(info.extent[0]) * int(info.extent[1]) == space
+    assert info.table == knn.KNN_TABLE_HASH
+    assert_same(got, oracle_run(x, lab, q, 1.0, 5, knn.KNN_VOTE), knn.KNN_VOTE)
+
+
 def test_clustered_heavy_cells():
     """Tight clusters: cells with thousands of points next to near-empty space."""
     w = wl.make("skewed_reg", n=200_000, m=3000, w=0.02)
