@@ -198,6 +198,25 @@ constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kRadixMax = 512;
 
+// Lanes of the warp whose digit (BITS bits) equals this lane's, among the
+// lanes in `valid`: one ballot per digit bit.
+template <int BITS>
+__device__ __forceinline__ unsigned match_digit(unsigned d, unsigned valid)
+{
+    unsigned m = valid;
+#pragma unroll
+    for (int b = 0; b < BITS; ++b) {
+        const bool bit = (d >> b) & 1u;
+        const unsigned bal = __ballot_sync(FULL, bit);
+        m &= bit ? bal : ~bal;
+    }
+    return m;
+}
+template <int R>
+struct DigitBits {
+    static constexpr int value = R == 512 ? 9 : 8;
+};
+
 template <class K, int R>
 __global__ void __launch_bounds__(kSortThreads)
     radix_hist_kernel(const K* __restrict__ keys, long long n, int shift,
@@ -212,9 +231,8 @@ __global__ void __launch_bounds__(kSortThreads)
     for (int r = 0; r < kSortItems; ++r) {
         const long long i = base + r * kSortThreads + t;
         const bool valid = i < n;
-        const unsigned dg =
-            valid ? (unsigned)((keys[i] >> shift) & (K)(R - 1)) : R + (t & 31);
-        const unsigned peers = __match_any_sync(FULL, dg);
+        const unsigned dg = valid ? (unsigned)((keys[i] >> shift) & (K)(R - 1)) : 0u;
+        const unsigned peers = match_digit<DigitBits<R>::value>(dg, __ballot_sync(FULL, valid));
         if (valid && (peers & lanemask_lt()) == 0u) atomicAdd(&cnt[dg], __popc(peers));
     }
     __syncthreads();
@@ -255,7 +273,8 @@ __global__ void __launch_bounds__(kSortThreads)
         k[r] = valid ? kin[tile + local] : (K)0;
         v[r] = valid ? vin[tile + local] : 0u;
         const unsigned d = valid ? (unsigned)((k[r] >> shift) & MASK) : R + lane;
-        const unsigned peers = __match_any_sync(FULL, d);
+        const unsigned peers =
+            match_digit<DigitBits<R>::value>(d & (unsigned)(R - 1), __ballot_sync(FULL, valid));
         const unsigned before = __popc(peers & lanemask_lt());
         unsigned int b = 0u;
         if (valid) b = wcnt[warp][d];
