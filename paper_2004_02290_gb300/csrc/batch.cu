@@ -618,7 +618,7 @@ knn_status batch_build_impl(int count, const float* const* points, const void* c
 
         // ---- keys, sort, cells ----
         unsigned long long *ka, *kb, *sk;
-        unsigned int *va, *vb, *sv, *flags, *cid, *cell_start;
+        unsigned int *va, *vb, *sv, *cell_start;
         unsigned long long* cell_key;
         void *rtmp, *stmp;
         const long long scan_n = std::max(total, dense_total);
@@ -627,8 +627,6 @@ knn_status batch_build_impl(int count, const float* const* points, const void* c
             (st = sc.alloc(&va, total, "batch rows")) != KNN_OK ||
             (st = sc.alloc(&vb, total, "batch rows")) != KNN_OK ||
             (st = sc.alloc(reinterpret_cast<char**>(&rtmp), radix_temp_bytes(total), "batch sort")) != KNN_OK ||
-            (st = sc.alloc(&flags, total, "batch cell flags")) != KNN_OK ||
-            (st = sc.alloc(&cid, total, "batch cell ids")) != KNN_OK ||
             (st = sc.alloc(reinterpret_cast<char**>(&stmp), scan_temp_bytes(scan_n), "batch scan")) != KNN_OK ||
             (st = sc.alloc(&cell_key, total, "batch cell keys")) != KNN_OK ||
             (st = sc.alloc(&cell_start, total + 1, "batch cell starts")) != KNN_OK)
@@ -640,7 +638,7 @@ knn_status batch_build_impl(int count, const float* const* points, const void* c
         count_launches(1);
         e = radix_sort_pairs(ka, va, kb, vb, total, shift + ib, rtmp, &sk, &sv, s);
         if (e == cudaSuccess)
-            e = launch_cells(sk, total, flags, cid, stmp, cell_key, cell_start, b->gdev, s);
+            e = launch_cells(sk, total, stmp, cell_key, cell_start, b->gdev, s);
         if (e != cudaSuccess) return bail(cuda_error(e, "batch sort"));
 
         // ---- tables ----

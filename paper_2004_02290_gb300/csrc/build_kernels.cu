@@ -166,23 +166,39 @@ __global__ void __launch_bounds__(kBoxFinalThreads)
 // clamped to split_j - 1 on a grid with splits, then the linear id
 // sum_j c_j * stride_j; the value is the point's index.
 // ---------------------------------------------------------------------------
+constexpr int kKeyUnroll = 4;
+
 template <int D, class K>
 __global__ void cell_keys_kernel(const float* __restrict__ pts, long long n, GridConst g,
                                  K* __restrict__ keys,
                                  unsigned int* __restrict__ vals)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        unsigned long long key = 0;
+    // kKeyUnroll points a thread per round, all of their loads issued first
+    for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < n;
+         i0 += kKeyUnroll * stride) {
+        float p[kKeyUnroll][D];
 #pragma unroll
-        for (int j = 0; j < D; ++j) {
-            const float t = __fdiv_rn(__fsub_rn(__ldg(pts + i * D + j), g.lo[j]), g.w[j]);
-            long long c = (long long)floorf(t);
-            if (g.split[j] > 0 && c > g.split[j] - 1) c = g.split[j] - 1;
-            key += (unsigned long long)c * g.stride[j];
+        for (int u = 0; u < kKeyUnroll; ++u) {
+            const long long i = i0 + u * stride;
+#pragma unroll
+            for (int j = 0; j < D; ++j) p[u][j] = i < n ? __ldg(pts + i * D + j) : 0.0f;
         }
-        keys[i] = (K)key;  // 32-bit K only when every id of the box fits
-        vals[i] = (unsigned int)i;
+#pragma unroll
+        for (int u = 0; u < kKeyUnroll; ++u) {
+            const long long i = i0 + u * stride;
+            if (i >= n) break;
+            unsigned long long key = 0;
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                const float t = __fdiv_rn(__fsub_rn(p[u][j], g.lo[j]), g.w[j]);
+                long long c = (long long)floorf(t);
+                if (g.split[j] > 0 && c > g.split[j] - 1) c = g.split[j] - 1;
+                key += (unsigned long long)c * g.stride[j];
+            }
+            keys[i] = (K)key;  // 32-bit K only when every id of the box fits
+            vals[i] = (unsigned int)i;
+        }
     }
 }
 
@@ -222,25 +238,34 @@ __global__ void __launch_bounds__(kSortThreads)
     radix_hist_kernel(const K* __restrict__ keys, long long n, int shift,
                       unsigned int* __restrict__ hist, unsigned int nb)
 {
-    __shared__ unsigned int cnt[R];
-    const int t = threadIdx.x;
-    for (int e = t; e < R; e += kSortThreads) cnt[e] = 0u;
+    constexpr int W = kSortThreads / 32;
+    __shared__ unsigned int cnt[W][R];  // one histogram per warp
+    const int t = threadIdx.x, warp = t >> 5;
+    for (int e = t; e < W * R; e += kSortThreads) (&cnt[0][0])[e] = 0u;
     __syncthreads();
     const long long base = (long long)blockIdx.x * kSortTile;
+    K kv[kSortItems];
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         const long long i = base + r * kSortThreads + t;
-        const bool valid = i < n;
-        const unsigned dg = valid ? (unsigned)((keys[i] >> shift) & (K)(R - 1)) : 0u;
-        const unsigned peers = match_digit<DigitBits<R>::value>(dg, __ballot_sync(FULL, valid));
-        if (valid && (peers & lanemask_lt()) == 0u) atomicAdd(&cnt[dg], __popc(peers));
+        kv[r] = i < n ? keys[i] : (K)0;
+    }
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const long long i = base + r * kSortThreads + t;
+        if (i < n) atomicAdd(&cnt[warp][(unsigned)((kv[r] >> shift) & (K)(R - 1))], 1u);
     }
     __syncthreads();
-    for (int e = t; e < R; e += kSortThreads) hist[(size_t)e * nb + blockIdx.x] = cnt[e];
+    for (int e = t; e < R; e += kSortThreads) {
+        unsigned int c = 0u;
+#pragma unroll
+        for (int w = 0; w < W; ++w) c += cnt[w][e];
+        hist[(size_t)e * nb + blockIdx.x] = c;
+    }
 }
 
 template <class K, int R>
-__global__ void __launch_bounds__(kSortThreads)
+__global__ void __launch_bounds__(kSortThreads, (sizeof(K) == 4 ? 5 : 4))
     radix_scatter_kernel(const K* __restrict__ kin, const unsigned int* __restrict__ vin,
                          K* __restrict__ kout, unsigned int* __restrict__ vout,
                          long long n, int shift, const unsigned int* __restrict__ scanned,
@@ -257,21 +282,31 @@ __global__ void __launch_bounds__(kSortThreads)
     __shared__ unsigned int sval[kSortTile];
 
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    // this thread's digits' global bases, loaded now and stored after the
+    // ranking so that their latency overlaps it
+    unsigned int gb[DPT];
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) gb[q] = scanned[(size_t)(t * DPT + q) * nb + blockIdx.x];
     for (int e = t; e < W * R; e += kSortThreads) (&wcnt[0][0])[e] = 0u;
-    for (int e = t; e < R; e += kSortThreads) gbase[e] = scanned[(size_t)e * nb + blockIdx.x];
-    __syncthreads();
 
     const long long tile = (long long)blockIdx.x * kSortTile;
     const long long count = n - tile < kSortTile ? n - tile : kSortTile;
     K k[kSortItems];
     unsigned int v[kSortItems], rank[kSortItems], dg[kSortItems];
-    // warp `warp` ranks elements [warp*256, warp*256+256) of the tile, in order
+    // warp `warp` ranks elements [warp*256, warp*256+256) of the tile, in
+    // order; all of its loads are issued first
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         const int local = warp * (32 * kSortItems) + r * 32 + lane;
         const bool valid = local < count;
         k[r] = valid ? kin[tile + local] : (K)0;
         v[r] = valid ? vin[tile + local] : 0u;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const int local = warp * (32 * kSortItems) + r * 32 + lane;
+        const bool valid = local < count;
         const unsigned d = valid ? (unsigned)((k[r] >> shift) & MASK) : R + lane;
         const unsigned peers =
             match_digit<DigitBits<R>::value>(d & (unsigned)(R - 1), __ballot_sync(FULL, valid));
@@ -317,6 +352,7 @@ __global__ void __launch_bounds__(kSortThreads)
 #pragma unroll
     for (int q = 0; q < DPT; ++q) {
         dig_off[t * DPT + q] = off;
+        gbase[t * DPT + q] = gb[q];
         off += run[q];
     }
     __syncthreads();
@@ -429,37 +465,75 @@ __global__ void __launch_bounds__(kScanThreads)
 }
 
 // ---------------------------------------------------------------------------
-// Cells: a head flag where the sorted id changes; the exclusive scan of the
-// flags numbers the cells.  Each head writes its cell's id and first row.
+// Cells: a head where the sorted id changes (and at row 0); the exclusive
+// scan of the heads numbers the cells, and each head writes its cell's id and
+// first row.  Both passes of the scan (per-block head counts, then the
+// scan proper) recompute the heads from the sorted keys, so no flag or cell
+// index array is written.  Blocks of kScanBlock rows, kScanItems consecutive
+// rows a thread.
 // ---------------------------------------------------------------------------
 template <class K>
-__global__ void head_flags_kernel(const K* __restrict__ keys, long long n,
-                                  unsigned int* __restrict__ flags)
+__device__ __forceinline__ unsigned int heads_of(const K* __restrict__ keys, long long n,
+                                                 long long base, K (&kv)[kScanItems],
+                                                 unsigned int (&head)[kScanItems])
 {
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-        flags[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
+    K prev = base > 0 && base <= n ? keys[base - 1] : (K)0;
+    unsigned int cnt = 0u;
+#pragma unroll
+    for (int r = 0; r < kScanItems; ++r) kv[r] = base + r < n ? keys[base + r] : (K)0;
+#pragma unroll
+    for (int r = 0; r < kScanItems; ++r) {
+        const long long i = base + r;
+        head[r] = i < n && (i == 0 || kv[r] != prev) ? 1u : 0u;
+        prev = kv[r];
+        cnt += head[r];
+    }
+    return cnt;
 }
 
 template <class K>
-__global__ void cells_write_kernel(const K* __restrict__ keys, long long n,
-                                   const unsigned int* __restrict__ flags,
-                                   const unsigned int* __restrict__ cid,
-                                   unsigned long long* __restrict__ cell_key,
-                                   unsigned int* __restrict__ cell_start, GridDev* gdev)
+__global__ void __launch_bounds__(kScanThreads)
+    cells_count_kernel(const K* __restrict__ keys, long long n, unsigned int* __restrict__ sums)
 {
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        if (flags[i]) {
-            cell_key[cid[i]] = (unsigned long long)keys[i];
-            cell_start[cid[i]] = (unsigned int)i;
+    __shared__ unsigned int wsum[32];
+    const long long base = (long long)blockIdx.x * kScanBlock + threadIdx.x * kScanItems;
+    K kv[kScanItems];
+    unsigned int head[kScanItems];
+    const unsigned int cnt = heads_of(keys, n, base, kv, head);
+    unsigned int total;
+    block_scan_incl(cnt, wsum, &total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+template <class K>
+__global__ void __launch_bounds__(kScanThreads)
+    cells_write_kernel(const K* __restrict__ keys, long long n,
+                       const unsigned int* __restrict__ sums,
+                       unsigned long long* __restrict__ cell_key,
+                       unsigned int* __restrict__ cell_start, GridDev* gdev)
+{
+    __shared__ unsigned int wsum[32];
+    const long long base = (long long)blockIdx.x * kScanBlock + threadIdx.x * kScanItems;
+    K kv[kScanItems];
+    unsigned int head[kScanItems];
+    const unsigned int cnt = heads_of(keys, n, base, kv, head);
+    unsigned int total;
+    // the first cell this thread's rows open
+    unsigned int c = block_scan_incl(cnt, wsum, &total) - cnt + sums[blockIdx.x];
+#pragma unroll
+    for (int r = 0; r < kScanItems; ++r) {
+        const long long i = base + r;
+        if (head[r]) {
+            cell_key[c] = (unsigned long long)kv[r];
+            cell_start[c] = (unsigned int)i;
+            ++c;
         }
         if (i == n - 1) {
-            const unsigned long long u = cid[i] + flags[i];
-            cell_start[u] = (unsigned int)n;
+            // c is now the number of cells
+            cell_start[c] = (unsigned int)n;
             unsigned long long cap = 16ull;
-            while (cap < 2ull * u) cap <<= 1;
-            gdev->ncells = u;
+            while (cap < 2ull * c) cap <<= 1;
+            gdev->ncells = c;
             gdev->hmask = cap - 1ull;
         }
     }
@@ -778,36 +852,34 @@ cudaError_t radix_sort_pairs(unsigned int* keys_a, unsigned int* vals_a, unsigne
 
 namespace {
 template <class K>
-cudaError_t launch_cells_t(const K* sorted_keys, long long n, unsigned int* flags_tmp,
-                           unsigned int* cid_tmp, void* scan_tmp, unsigned long long* cell_key,
-                           unsigned int* cell_start, GridDev* gdev, cudaStream_t s)
+cudaError_t launch_cells_t(const K* sorted_keys, long long n, void* scan_tmp,
+                           unsigned long long* cell_key, unsigned int* cell_start, GridDev* gdev,
+                           cudaStream_t s)
 {
-    const int b = grid_for(n, 256);
-    head_flags_kernel<K><<<b, 256, 0, s>>>(sorted_keys, n, flags_tmp);
-    cudaError_t e = scan_exclusive(flags_tmp, cid_tmp, n, scan_tmp, s);
-    if (e != cudaSuccess) return e;
-    cells_write_kernel<K><<<b, 256, 0, s>>>(sorted_keys, n, flags_tmp, cid_tmp, cell_key,
-                                            cell_start, gdev);
-    count_launches(2);
+    if (n <= 0) return cudaSuccess;
+    const long long nb = (n + kScanBlock - 1) / kScanBlock;
+    unsigned int* sums = static_cast<unsigned int*>(scan_tmp);
+    cells_count_kernel<K><<<(unsigned)nb, kScanThreads, 0, s>>>(sorted_keys, n, sums);
+    scan_spine_kernel<<<1, 1024, 0, s>>>(sums, nb);
+    cells_write_kernel<K><<<(unsigned)nb, kScanThreads, 0, s>>>(sorted_keys, n, sums, cell_key,
+                                                                cell_start, gdev);
+    count_launches(3);
     return cudaGetLastError();
 }
 }  // namespace
 
-cudaError_t launch_cells(const unsigned long long* sorted_keys, long long n,
-                         unsigned int* flags_tmp, unsigned int* cid_tmp, void* scan_tmp,
+cudaError_t launch_cells(const unsigned long long* sorted_keys, long long n, void* scan_tmp,
                          unsigned long long* cell_key, unsigned int* cell_start, GridDev* gdev,
                          cudaStream_t s)
 {
-    return launch_cells_t(sorted_keys, n, flags_tmp, cid_tmp, scan_tmp, cell_key, cell_start,
-                          gdev, s);
+    return launch_cells_t(sorted_keys, n, scan_tmp, cell_key, cell_start, gdev, s);
 }
 
-cudaError_t launch_cells(const unsigned int* sorted_keys, long long n, unsigned int* flags_tmp,
-                         unsigned int* cid_tmp, void* scan_tmp, unsigned long long* cell_key,
-                         unsigned int* cell_start, GridDev* gdev, cudaStream_t s)
+cudaError_t launch_cells(const unsigned int* sorted_keys, long long n, void* scan_tmp,
+                         unsigned long long* cell_key, unsigned int* cell_start, GridDev* gdev,
+                         cudaStream_t s)
 {
-    return launch_cells_t(sorted_keys, n, flags_tmp, cid_tmp, scan_tmp, cell_key, cell_start,
-                          gdev, s);
+    return launch_cells_t(sorted_keys, n, scan_tmp, cell_key, cell_start, gdev, s);
 }
 
 cudaError_t launch_dense_table(const unsigned long long* cell_key, const unsigned int* cell_start,

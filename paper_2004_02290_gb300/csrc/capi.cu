@@ -390,7 +390,6 @@ knn_status build_impl(const float* points_user, const void* labels_user, long lo
         char *ka = nullptr, *kb = nullptr;
         unsigned int *va = nullptr, *vb = nullptr;
         void* rtmp = nullptr;
-        unsigned int *flags = nullptr, *cid = nullptr;
         void* stmp = nullptr;
         unsigned long long* cell_key = nullptr;
         unsigned int* cell_start = nullptr;
@@ -439,19 +438,17 @@ knn_status build_impl(const float* points_user, const void* labels_user, long lo
         const unsigned long long scan_n =
             table == KNN_TABLE_DENSE && space + 1ull > (unsigned long long)n ? space + 1ull
                                                                            : (unsigned long long)n;
-        st = tmp.alloc(&flags, (size_t)n, "cell flags");
-        if (st == KNN_OK) st = tmp.alloc(&cid, (size_t)n, "cell ids");
-        if (st == KNN_OK) st = tmp.alloc(reinterpret_cast<char**>(&stmp), scan_temp_bytes((long long)scan_n), "scan temp");
+        st = tmp.alloc(reinterpret_cast<char**>(&stmp), scan_temp_bytes((long long)scan_n), "scan temp");
         if (st == KNN_OK) st = tmp.alloc(&cell_key, (size_t)n, "cell keys");
         if (st == KNN_OK) st = tmp.alloc(&cell_start, (size_t)n + 1, "cell starts");
         if (st == KNN_OK) st = dalloc(&x->gdev, 1, s, "grid");
         if (st != KNN_OK) {
             return fail(st);
         }
-        e = narrow ? launch_cells(static_cast<const unsigned int*>(sk), n, flags, cid, stmp, cell_key,
-                                  cell_start, x->gdev, s)
-                   : launch_cells(static_cast<const unsigned long long*>(sk), n, flags, cid, stmp,
-                                  cell_key, cell_start, x->gdev, s);
+        e = narrow ? launch_cells(static_cast<const unsigned int*>(sk), n, stmp, cell_key, cell_start,
+                                  x->gdev, s)
+                   : launch_cells(static_cast<const unsigned long long*>(sk), n, stmp, cell_key,
+                                  cell_start, x->gdev, s);
         if (e != cudaSuccess) {
             return fail(cuda_fail(e, "cells"));
         }

@@ -97,13 +97,14 @@ size_t scan_temp_bytes(long long n);
 cudaError_t scan_exclusive(const unsigned int* in, unsigned int* out, long long n, void* temp,
                            cudaStream_t s);
 
-cudaError_t launch_cells(const unsigned long long* sorted_keys, long long n,
-                         unsigned int* flags_tmp, unsigned int* cid_tmp, void* scan_tmp,
+// Cells of n sorted keys: cell_key[c] / cell_start[c] for every cell c,
+// cell_start[U] = n, and gdev->ncells / hmask.  scan_tmp: scan_temp_bytes(n).
+cudaError_t launch_cells(const unsigned long long* sorted_keys, long long n, void* scan_tmp,
                          unsigned long long* cell_key, unsigned int* cell_start, GridDev* gdev,
                          cudaStream_t s);
-cudaError_t launch_cells(const unsigned int* sorted_keys, long long n, unsigned int* flags_tmp,
-                         unsigned int* cid_tmp, void* scan_tmp, unsigned long long* cell_key,
-                         unsigned int* cell_start, GridDev* gdev, cudaStream_t s);
+cudaError_t launch_cells(const unsigned int* sorted_keys, long long n, void* scan_tmp,
+                         unsigned long long* cell_key, unsigned int* cell_start, GridDev* gdev,
+                         cudaStream_t s);
 
 // Dense table: dstart[id] = first row of cell id, for every id of the box, and
 // dstart[ncell_space] = n.  scan_tmp: scan_temp_bytes(ncell_space + 1).
