@@ -170,8 +170,7 @@ constexpr int kKeyUnroll = 4;
 
 template <int D, class K>
 __global__ void cell_keys_kernel(const float* __restrict__ pts, long long n, GridConst g,
-                                 K* __restrict__ keys,
-                                 unsigned int* __restrict__ vals)
+                                 K* __restrict__ keys)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     // kKeyUnroll points a thread per round, all of their loads issued first
@@ -197,7 +196,6 @@ __global__ void cell_keys_kernel(const float* __restrict__ pts, long long n, Gri
                 key += (unsigned long long)c * g.stride[j];
             }
             keys[i] = (K)key;  // 32-bit K only when every id of the box fits
-            vals[i] = (unsigned int)i;
         }
     }
 }
@@ -300,7 +298,7 @@ __global__ void __launch_bounds__(kSortThreads, (sizeof(K) == 4 ? 5 : 4))
         const int local = warp * (32 * kSortItems) + r * 32 + lane;
         const bool valid = local < count;
         k[r] = valid ? kin[tile + local] : (K)0;
-        v[r] = valid ? vin[tile + local] : 0u;
+        v[r] = valid ? (vin ? vin[tile + local] : (unsigned int)(tile + local)) : 0u;
     }
     __syncthreads();
 #pragma unroll
@@ -372,6 +370,14 @@ __global__ void __launch_bounds__(kSortThreads, (sizeof(K) == 4 ? 5 : 4))
         kout[g] = key;
         vout[g] = sval[i];
     }
+}
+
+// vals[i] = i: the values of a sort whose first pass did not run.
+__global__ void iota_kernel(unsigned int* __restrict__ vals, long long n)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        vals[i] = (unsigned int)i;
 }
 
 // ---------------------------------------------------------------------------
@@ -633,8 +639,7 @@ __global__ void gather_kernel(const float* __restrict__ pts, long long n,
 // Cell id of each query clamped into the box (for the locality order only).
 template <int D, class K>
 __global__ void query_keys_kernel(const float* __restrict__ q, long long m, GridConst g,
-                                  K* __restrict__ keys,
-                                  unsigned int* __restrict__ vals)
+                                  K* __restrict__ keys)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
@@ -648,7 +653,6 @@ __global__ void query_keys_kernel(const float* __restrict__ q, long long m, Grid
             key += (unsigned long long)c * g.stride[j];
         }
         keys[i] = (K)key;  // 32-bit K only when every id of the box fits
-        vals[i] = (unsigned int)i;
     }
 }
 
@@ -688,19 +692,19 @@ cudaError_t launch_box(const float* pts, long long n, int d, const Widths& w, fl
 namespace {
 template <class K>
 cudaError_t launch_cell_keys_t(const float* pts, long long n, const GridConst& g, K* keys,
-                                unsigned int* vals, cudaStream_t s)
+                               cudaStream_t s)
 {
     const int b = grid_for(n, 256);
     count_launches(1);
     switch (g.d) {
-    case 1: cell_keys_kernel<1, K><<<b, 256, 0, s>>>(pts, n, g, keys, vals); break;
-    case 2: cell_keys_kernel<2, K><<<b, 256, 0, s>>>(pts, n, g, keys, vals); break;
-    case 3: cell_keys_kernel<3, K><<<b, 256, 0, s>>>(pts, n, g, keys, vals); break;
-    case 4: cell_keys_kernel<4, K><<<b, 256, 0, s>>>(pts, n, g, keys, vals); break;
-    case 5: cell_keys_kernel<5, K><<<b, 256, 0, s>>>(pts, n, g, keys, vals); break;
-    case 6: cell_keys_kernel<6, K><<<b, 256, 0, s>>>(pts, n, g, keys, vals); break;
-    case 7: cell_keys_kernel<7, K><<<b, 256, 0, s>>>(pts, n, g, keys, vals); break;
-    case 8: cell_keys_kernel<8, K><<<b, 256, 0, s>>>(pts, n, g, keys, vals); break;
+    case 1: cell_keys_kernel<1, K><<<b, 256, 0, s>>>(pts, n, g, keys); break;
+    case 2: cell_keys_kernel<2, K><<<b, 256, 0, s>>>(pts, n, g, keys); break;
+    case 3: cell_keys_kernel<3, K><<<b, 256, 0, s>>>(pts, n, g, keys); break;
+    case 4: cell_keys_kernel<4, K><<<b, 256, 0, s>>>(pts, n, g, keys); break;
+    case 5: cell_keys_kernel<5, K><<<b, 256, 0, s>>>(pts, n, g, keys); break;
+    case 6: cell_keys_kernel<6, K><<<b, 256, 0, s>>>(pts, n, g, keys); break;
+    case 7: cell_keys_kernel<7, K><<<b, 256, 0, s>>>(pts, n, g, keys); break;
+    case 8: cell_keys_kernel<8, K><<<b, 256, 0, s>>>(pts, n, g, keys); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -708,33 +712,33 @@ cudaError_t launch_cell_keys_t(const float* pts, long long n, const GridConst& g
 }  // namespace
 
 cudaError_t launch_cell_keys(const float* pts, long long n, const GridConst& g,
-                             unsigned long long* keys, unsigned int* vals, cudaStream_t s)
+                             unsigned long long* keys, cudaStream_t s)
 {
-    return launch_cell_keys_t(pts, n, g, keys, vals, s);
+    return launch_cell_keys_t(pts, n, g, keys, s);
 }
 
 cudaError_t launch_cell_keys(const float* pts, long long n, const GridConst& g, unsigned int* keys,
-                             unsigned int* vals, cudaStream_t s)
+                             cudaStream_t s)
 {
-    return launch_cell_keys_t(pts, n, g, keys, vals, s);
+    return launch_cell_keys_t(pts, n, g, keys, s);
 }
 
 namespace {
 template <class K>
 cudaError_t launch_query_keys_t(const float* q, long long m, const GridConst& g, K* keys,
-                                 unsigned int* vals, cudaStream_t s)
+                                cudaStream_t s)
 {
     const int b = grid_for(m, 256);
     count_launches(1);
     switch (g.d) {
-    case 1: query_keys_kernel<1, K><<<b, 256, 0, s>>>(q, m, g, keys, vals); break;
-    case 2: query_keys_kernel<2, K><<<b, 256, 0, s>>>(q, m, g, keys, vals); break;
-    case 3: query_keys_kernel<3, K><<<b, 256, 0, s>>>(q, m, g, keys, vals); break;
-    case 4: query_keys_kernel<4, K><<<b, 256, 0, s>>>(q, m, g, keys, vals); break;
-    case 5: query_keys_kernel<5, K><<<b, 256, 0, s>>>(q, m, g, keys, vals); break;
-    case 6: query_keys_kernel<6, K><<<b, 256, 0, s>>>(q, m, g, keys, vals); break;
-    case 7: query_keys_kernel<7, K><<<b, 256, 0, s>>>(q, m, g, keys, vals); break;
-    case 8: query_keys_kernel<8, K><<<b, 256, 0, s>>>(q, m, g, keys, vals); break;
+    case 1: query_keys_kernel<1, K><<<b, 256, 0, s>>>(q, m, g, keys); break;
+    case 2: query_keys_kernel<2, K><<<b, 256, 0, s>>>(q, m, g, keys); break;
+    case 3: query_keys_kernel<3, K><<<b, 256, 0, s>>>(q, m, g, keys); break;
+    case 4: query_keys_kernel<4, K><<<b, 256, 0, s>>>(q, m, g, keys); break;
+    case 5: query_keys_kernel<5, K><<<b, 256, 0, s>>>(q, m, g, keys); break;
+    case 6: query_keys_kernel<6, K><<<b, 256, 0, s>>>(q, m, g, keys); break;
+    case 7: query_keys_kernel<7, K><<<b, 256, 0, s>>>(q, m, g, keys); break;
+    case 8: query_keys_kernel<8, K><<<b, 256, 0, s>>>(q, m, g, keys); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -742,15 +746,15 @@ cudaError_t launch_query_keys_t(const float* q, long long m, const GridConst& g,
 }  // namespace
 
 cudaError_t launch_query_keys(const float* q, long long m, const GridConst& g,
-                              unsigned long long* keys, unsigned int* vals, cudaStream_t s)
+                              unsigned long long* keys, cudaStream_t s)
 {
-    return launch_query_keys_t(q, m, g, keys, vals, s);
+    return launch_query_keys_t(q, m, g, keys, s);
 }
 
 cudaError_t launch_query_keys(const float* q, long long m, const GridConst& g, unsigned int* keys,
-                              unsigned int* vals, cudaStream_t s)
+                              cudaStream_t s)
 {
-    return launch_query_keys_t(q, m, g, keys, vals, s);
+    return launch_query_keys_t(q, m, g, keys, s);
 }
 
 size_t scan_temp_bytes(long long n)
@@ -785,7 +789,7 @@ namespace {
 template <class K>
 cudaError_t radix_sort_pairs_t(K* keys_a, unsigned int* vals_a, K* keys_b, unsigned int* vals_b,
                                long long n, int bits, void* temp, K** result_keys,
-                               unsigned int** result_vals, cudaStream_t s)
+                               unsigned int** result_vals, cudaStream_t s, bool identity_vals)
 {
     const long long nb = (n + kSortTile - 1) / kSortTile;
     unsigned int* hist = static_cast<unsigned int*>(temp);
@@ -800,9 +804,16 @@ cudaError_t radix_sort_pairs_t(K* keys_a, unsigned int* vals_a, K* keys_b, unsig
     const int passes = p9 < p8 ? p9 : p8;
     const int wide = p9 < p8 ? bits - 8 * passes : 0;
     int shift = 0;
+    // with identity_vals the first pass makes the values (each element's
+    // index) instead of reading them
+    if (identity_vals && (passes == 0 || n <= 1)) {
+        iota_kernel<<<grid_for(n, 256), 256, 0, s>>>(vals_a, n);
+        count_launches(1);
+    }
     for (int pass = 0; pass < passes && n > 1; ++pass) {
         const bool w9 = pass >= passes - wide;
         const long long entries = nb * (w9 ? 512 : 256);
+        const unsigned int* src = pass == 0 && identity_vals ? nullptr : vin;
         if (w9)
             radix_hist_kernel<K, 512><<<(unsigned)nb, kSortThreads, 0, s>>>(kin, n, shift, hist,
                                                                           (unsigned)nb);
@@ -813,10 +824,10 @@ cudaError_t radix_sort_pairs_t(K* keys_a, unsigned int* vals_a, K* keys_b, unsig
         if (e != cudaSuccess) return e;
         if (w9)
             radix_scatter_kernel<K, 512><<<(unsigned)nb, kSortThreads, 0, s>>>(
-                kin, vin, kout, vout, n, shift, hist, (unsigned)nb);
+                kin, src, kout, vout, n, shift, hist, (unsigned)nb);
         else
             radix_scatter_kernel<K, 256><<<(unsigned)nb, kSortThreads, 0, s>>>(
-                kin, vin, kout, vout, n, shift, hist, (unsigned)nb);
+                kin, src, kout, vout, n, shift, hist, (unsigned)nb);
         shift += w9 ? 9 : 8;
         count_launches(2);
         K* tk = kin;
@@ -835,19 +846,19 @@ cudaError_t radix_sort_pairs_t(K* keys_a, unsigned int* vals_a, K* keys_b, unsig
 cudaError_t radix_sort_pairs(unsigned long long* keys_a, unsigned int* vals_a,
                              unsigned long long* keys_b, unsigned int* vals_b, long long n,
                              int bits, void* temp, unsigned long long** result_keys,
-                             unsigned int** result_vals, cudaStream_t s)
+                             unsigned int** result_vals, cudaStream_t s, bool identity_vals)
 {
     return radix_sort_pairs_t(keys_a, vals_a, keys_b, vals_b, n, bits, temp, result_keys,
-                              result_vals, s);
+                              result_vals, s, identity_vals);
 }
 
 cudaError_t radix_sort_pairs(unsigned int* keys_a, unsigned int* vals_a, unsigned int* keys_b,
                              unsigned int* vals_b, long long n, int bits, void* temp,
                              unsigned int** result_keys, unsigned int** result_vals,
-                             cudaStream_t s)
+                             cudaStream_t s, bool identity_vals)
 {
     return radix_sort_pairs_t(keys_a, vals_a, keys_b, vals_b, n, bits, temp, result_keys,
-                              result_vals, s);
+                              result_vals, s, identity_vals);
 }
 
 namespace {

@@ -409,17 +409,19 @@ knn_status build_impl(const float* points_user, const void* labels_user, long lo
         if (narrow) {
             auto k32a = reinterpret_cast<unsigned int*>(ka), k32b = reinterpret_cast<unsigned int*>(kb);
             unsigned int* sk32 = nullptr;
-            e = launch_cell_keys(pts, n, g, k32a, va, s);
+            e = launch_cell_keys(pts, n, g, k32a, s);
             g_timer.mark("keys", s);
-            if (e == cudaSuccess) e = radix_sort_pairs(k32a, va, k32b, vb, n, bits, rtmp, &sk32, &sv, s);
+            if (e == cudaSuccess)
+                e = radix_sort_pairs(k32a, va, k32b, vb, n, bits, rtmp, &sk32, &sv, s, true);
             sk = sk32;
         } else {
             auto k64a = reinterpret_cast<unsigned long long*>(ka);
             auto k64b = reinterpret_cast<unsigned long long*>(kb);
             unsigned long long* sk64 = nullptr;
-            e = launch_cell_keys(pts, n, g, k64a, va, s);
+            e = launch_cell_keys(pts, n, g, k64a, s);
             g_timer.mark("keys", s);
-            if (e == cudaSuccess) e = radix_sort_pairs(k64a, va, k64b, vb, n, bits, rtmp, &sk64, &sv, s);
+            if (e == cudaSuccess)
+                e = radix_sort_pairs(k64a, va, k64b, vb, n, bits, rtmp, &sk64, &sv, s, true);
             sk = sk64;
         }
         g_timer.mark("sort", s);
@@ -559,15 +561,17 @@ knn_status query_impl(const ghn_index* x, const float* queries_user, long long m
             if (narrow) {
                 auto k32a = reinterpret_cast<unsigned int*>(ka), k32b = reinterpret_cast<unsigned int*>(kb);
                 unsigned int* sk;
-                GHN_CHECK(launch_query_keys(q, m, x->g, k32a, va, s), "query keys");
-                GHN_CHECK(radix_sort_pairs(k32a, va, k32b, vb, m, x->key_bits, rtmp, &sk, &sv, s),
+                GHN_CHECK(launch_query_keys(q, m, x->g, k32a, s), "query keys");
+                GHN_CHECK(radix_sort_pairs(k32a, va, k32b, vb, m, x->key_bits, rtmp, &sk, &sv, s,
+                                           true),
                           "query order");
             } else {
                 auto k64a = reinterpret_cast<unsigned long long*>(ka);
                 auto k64b = reinterpret_cast<unsigned long long*>(kb);
                 unsigned long long* sk;
-                GHN_CHECK(launch_query_keys(q, m, x->g, k64a, va, s), "query keys");
-                GHN_CHECK(radix_sort_pairs(k64a, va, k64b, vb, m, x->key_bits, rtmp, &sk, &sv, s),
+                GHN_CHECK(launch_query_keys(q, m, x->g, k64a, s), "query keys");
+                GHN_CHECK(radix_sort_pairs(k64a, va, k64b, vb, m, x->key_bits, rtmp, &sk, &sv, s,
+                                           true),
                           "query order");
             }
             order = sv;

@@ -75,22 +75,27 @@ cudaError_t launch_box(const float* pts, long long n, int d, const Widths& w, fl
                        int partial_blocks, BoxOut* out, cudaStream_t s);
 int box_partial_blocks(long long n);
 
+// Eq. 1 cell id of every training point (32-bit keys only when every id of
+// the box fits).
 cudaError_t launch_cell_keys(const float* pts, long long n, const GridConst& g,
-                             unsigned long long* keys, unsigned int* vals, cudaStream_t s);
+                             unsigned long long* keys, cudaStream_t s);
 cudaError_t launch_cell_keys(const float* pts, long long n, const GridConst& g, unsigned int* keys,
-                             unsigned int* vals, cudaStream_t s);  // every id < 2^32
+                             cudaStream_t s);
 
 // LSD radix sort of (key, value) by the low `bits` bits of the key; stable.
 // Returns in *result_keys / *result_vals the buffers that hold the sorted data.
+// With identity_vals the values are taken to be 0..n-1 and vals_a is not read
+// (it is still written, as one of the two value buffers).
 size_t radix_temp_bytes(long long n);
 cudaError_t radix_sort_pairs(unsigned long long* keys_a, unsigned int* vals_a,
                              unsigned long long* keys_b, unsigned int* vals_b, long long n,
                              int bits, void* temp, unsigned long long** result_keys,
-                             unsigned int** result_vals, cudaStream_t s);
+                             unsigned int** result_vals, cudaStream_t s,
+                             bool identity_vals = false);
 cudaError_t radix_sort_pairs(unsigned int* keys_a, unsigned int* vals_a, unsigned int* keys_b,
                              unsigned int* vals_b, long long n, int bits, void* temp,
                              unsigned int** result_keys, unsigned int** result_vals,
-                             cudaStream_t s);
+                             cudaStream_t s, bool identity_vals = false);
 
 // Exclusive prefix sum of n uint32 values (out may alias in).
 size_t scan_temp_bytes(long long n);
@@ -219,8 +224,8 @@ cudaError_t launch_query_d78(const QueryArgs& a, int sms, cudaStream_t s);
 
 // Query keys for the locality order (cell id of each query, clamped into the box).
 cudaError_t launch_query_keys(const float* q, long long m, const GridConst& g,
-                              unsigned long long* keys, unsigned int* vals, cudaStream_t s);
+                              unsigned long long* keys, cudaStream_t s);
 cudaError_t launch_query_keys(const float* q, long long m, const GridConst& g, unsigned int* keys,
-                              unsigned int* vals, cudaStream_t s);  // every id < 2^32
+                              cudaStream_t s);
 
 }  // namespace ghn
