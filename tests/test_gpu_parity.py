@@ -233,6 +233,28 @@ def test_cell_id_width_boundary(hi0, space, flags):
     assert_same(got, oracle_run(x, lab, q, 1.0, 5, knn.KNN_VOTE), knn.KNN_VOTE)
 
 
+@pytest.mark.parametrize("d,n", [(3, 4001), (5, 4003), (2, 3), (4, 4096)])
+@pytest.mark.parametrize("offset", [0, 1])
+def test_point_alignment_and_tails(d, n, offset):
+    """Points at a 16-byte boundary (the box and keys kernels load 4 points a
+    thread, the last n mod 4 one by one) and one float past it (the scalar
+    kernels)."""
+    x, lab, q = wl.uniform(n, 200, d, seed=40 + d)
+    buf = torch.zeros(n * d + offset, dtype=torch.float32, device="cuda")
+    buf[offset:] = torch.from_numpy(x).cuda().reshape(-1)
+    pts = buf[offset:].view(n, d)
+    assert (pts.data_ptr() % 16 == 0) == (offset == 0)
+    idx = knn.knn_build(pts, _dev(lab), 0.1)
+    ids, d2, pred = idx.query(_dev(q), 4, knn.KNN_VOTE, flags=knn.KNN_QUERY_CHECKED)
+    torch.cuda.synchronize()
+    info = idx.info()
+    g = oracle.Grid(x, lab, 0.1)
+    assert [float(info.origin[j]) for j in range(d)] == [float(v) for v in x.min(axis=0)]
+    got = (ids.cpu().numpy(), d2.cpu().numpy(), pred.cpu().numpy())
+    idx.free()
+    assert_same(got, g.query(q, 4, knn.KNN_VOTE), knn.KNN_VOTE)
+
+
 def test_clustered_heavy_cells():
     """Tight clusters: cells with thousands of points next to near-empty space."""
     w = wl.make("skewed_reg", n=200_000, m=3000, w=0.02)
