@@ -36,9 +36,11 @@ if ROOT not in sys.path:
 from paper_2004_02290_gb300 import workloads as wl  # noqa: E402
 
 METRIC = "queries/sec (index build + batched query per step)"
-# knn_query flags of the timed step (queries in input order: the locality sort
-# costs more than it saves on these workloads)
-QUERY_FLAGS = 0
+# Query order of the timed step per workload ("cell": KNN_QUERY_SORTED, the
+# queries grouped by cell before the search; "input": as given). The order
+# changes no result; "cell" is used where it saves more search time than it
+# costs (measured on GB300), else "input".
+QUERY_ORDER = {"skewed_reg": "cell"}
 UNIT = "queries/s"
 L2_FLUSH_BYTES = 512 << 20
 # ncu summary of the query kernel on a workload: profiles/query_kernel_<workload>_ncu.md
@@ -62,6 +64,8 @@ def parse_args(argv=None):
                    help="problems of the batched workload")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--query-order", choices=["auto", "input", "cell"], default="auto",
+                   help="visit queries as given or grouped by cell (auto: per workload)")
     p.add_argument("--cpu-sample", type=int, default=200_000,
                    help="queries of the oracle's bounded sample (per repetition)")
     p.add_argument("--cpu-seconds", type=float, default=8.0,
@@ -248,6 +252,15 @@ def run_reference(args):
     }), flush=True)
 
 
+def query_order(name: str, choice: str = "auto") -> str:
+    return QUERY_ORDER.get(name, "input") if choice == "auto" else choice
+
+
+def query_flags(knn, name: str, choice: str = "auto") -> int:
+    """knn_query flags of the timed step on workload `name`."""
+    return knn.KNN_QUERY_SORTED if query_order(name, choice) == "cell" else 0
+
+
 def workload_config(w: wl.Workload, l2: str):
     return {"workload": w.name, "n": w.n, "d": w.d, "m": w.m, "k": w.k,
             "mode": "vote" if w.mode == wl.VOTE else "mean", "cell_width": w.w,
@@ -394,7 +407,7 @@ def run_ours(args):
                            device=dev)
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     torch.cuda.synchronize(dev)
-    flags = QUERY_FLAGS
+    flags = query_flags(knn, w.name, args.query_order)
 
     def step(phases):
         idx = knn.knn_build(pts, lab, w.w, w.table, stream=stream)
@@ -501,6 +514,7 @@ def run_ours(args):
         "config": workload_config(w, "flushed before every step (512 MiB write)"),
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": int(launches),
+        "query_order": query_order(w.name, args.query_order),
         "phase_ms": {k: round(v, 4) for k, v in sorted(phase_ms.items())},
         "build_points_per_s": w.n / ((sum(v for k, v in phase_ms.items()
                                           if k.startswith("build."))) * 1e-3),
@@ -564,7 +578,8 @@ def run_e2e(w, knn, dev, args):
 
     def step():
         idx = knn.knn_build(pts, lab, w.w, w.table)
-        knn.knn_query(idx, q, w.k, w.mode, flags=QUERY_FLAGS, ids=ids, dist2=d2, pred=pred)
+        knn.knn_query(idx, q, w.k, w.mode, flags=query_flags(knn, w.name, args.query_order),
+                      ids=ids, dist2=d2, pred=pred)
         idx.free()
 
     for _ in range(2):

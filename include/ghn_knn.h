@@ -73,7 +73,8 @@ typedef int32_t knn_status;
 
 /* knn_query flags. */
 #define KNN_QUERY_CHECKED 1 /* synchronize `stream` and return the kernel's status */
-#define KNN_QUERY_SORTED 2  /* visit queries in cell order (locality in L2) */
+#define KNN_QUERY_SORTED 2  /* visit queries grouped by cell (locality in L2): ordered by the
+                              top 16 bits of their clamped cell id; results do not change */
 #define KNN_QUERY_EXACT 4   /* certified stop instead of the paper's rule: stop after
                                layer L once the k-th squared distance is below the
                                squared distance from the query to every cell outside

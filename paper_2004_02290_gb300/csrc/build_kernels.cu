@@ -802,7 +802,7 @@ __global__ void gather_kernel(const float* __restrict__ pts, long long n,
 
 // Cell id of each query clamped into the box (for the locality order only).
 template <int D, class K>
-__global__ void query_keys_kernel(const float* __restrict__ q, long long m, GridConst g,
+__global__ void query_keys_kernel(const float* __restrict__ q, long long m, GridConst g, int shift,
                                   K* __restrict__ keys)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -816,7 +816,7 @@ __global__ void query_keys_kernel(const float* __restrict__ q, long long m, Grid
             if (c > g.cmax[j]) c = g.cmax[j];
             key += (unsigned long long)c * g.stride[j];
         }
-        keys[i] = (K)key;  // 32-bit K only when every id of the box fits
+        keys[i] = (K)(key >> shift);  // 32-bit K only when every shifted id fits
     }
 }
 
@@ -921,36 +921,30 @@ cudaError_t launch_cell_keys(const float* pts, long long n, const GridConst& g, 
 
 namespace {
 template <class K>
-cudaError_t launch_query_keys_t(const float* q, long long m, const GridConst& g, K* keys,
-                                cudaStream_t s)
+cudaError_t launch_query_keys_t(const float* q, long long m, const GridConst& g, int shift,
+                                K* keys, cudaStream_t s)
 {
     const int b = grid_for(m, 256);
     count_launches(1);
     switch (g.d) {
-    case 1: query_keys_kernel<1, K><<<b, 256, 0, s>>>(q, m, g, keys); break;
-    case 2: query_keys_kernel<2, K><<<b, 256, 0, s>>>(q, m, g, keys); break;
-    case 3: query_keys_kernel<3, K><<<b, 256, 0, s>>>(q, m, g, keys); break;
-    case 4: query_keys_kernel<4, K><<<b, 256, 0, s>>>(q, m, g, keys); break;
-    case 5: query_keys_kernel<5, K><<<b, 256, 0, s>>>(q, m, g, keys); break;
-    case 6: query_keys_kernel<6, K><<<b, 256, 0, s>>>(q, m, g, keys); break;
-    case 7: query_keys_kernel<7, K><<<b, 256, 0, s>>>(q, m, g, keys); break;
-    case 8: query_keys_kernel<8, K><<<b, 256, 0, s>>>(q, m, g, keys); break;
+    case 1: query_keys_kernel<1, K><<<b, 256, 0, s>>>(q, m, g, shift, keys); break;
+    case 2: query_keys_kernel<2, K><<<b, 256, 0, s>>>(q, m, g, shift, keys); break;
+    case 3: query_keys_kernel<3, K><<<b, 256, 0, s>>>(q, m, g, shift, keys); break;
+    case 4: query_keys_kernel<4, K><<<b, 256, 0, s>>>(q, m, g, shift, keys); break;
+    case 5: query_keys_kernel<5, K><<<b, 256, 0, s>>>(q, m, g, shift, keys); break;
+    case 6: query_keys_kernel<6, K><<<b, 256, 0, s>>>(q, m, g, shift, keys); break;
+    case 7: query_keys_kernel<7, K><<<b, 256, 0, s>>>(q, m, g, shift, keys); break;
+    case 8: query_keys_kernel<8, K><<<b, 256, 0, s>>>(q, m, g, shift, keys); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 }  // namespace
 
-cudaError_t launch_query_keys(const float* q, long long m, const GridConst& g,
-                              unsigned long long* keys, cudaStream_t s)
+cudaError_t launch_query_keys(const float* q, long long m, const GridConst& g, int shift,
+                              unsigned int* keys, cudaStream_t s)
 {
-    return launch_query_keys_t(q, m, g, keys, s);
-}
-
-cudaError_t launch_query_keys(const float* q, long long m, const GridConst& g, unsigned int* keys,
-                              cudaStream_t s)
-{
-    return launch_query_keys_t(q, m, g, keys, s);
+    return launch_query_keys_t(q, m, g, shift, keys, s);
 }
 
 size_t scan_temp_bytes(long long n)

@@ -42,6 +42,10 @@ struct ghn_index {
 
 namespace {
 
+// Bits of the cell id that the locality order of the queries sorts by (the
+// top ones): two 8-bit radix passes.
+constexpr int kOrderBits = 16;
+
 thread_local char g_err[512] = "";
 
 void set_err(const char* fmt, ...)
@@ -545,35 +549,23 @@ knn_status query_impl(const ghn_index* x, const float* queries_user, long long m
 
         const unsigned int* order = nullptr;
         if ((flags & KNN_QUERY_SORTED) && m > 1 && x->key_bits > 0) {
-            // 32-bit keys when every cell id of the box fits
-            const bool narrow = x->key_bits <= 32;
-            const size_t key_bytes = narrow ? sizeof(unsigned int) : sizeof(unsigned long long);
-            char *ka = nullptr, *kb = nullptr;
+            // the order only has to bring queries of nearby cells together:
+            // sort by the top kOrderBits bits of the cell id (two 8-bit passes)
+            const int shift = x->key_bits > kOrderBits ? x->key_bits - kOrderBits : 0;
+            unsigned int *ka = nullptr, *kb = nullptr;
             unsigned int *va = nullptr, *vb = nullptr;
             char* rtmp = nullptr;
-            st = tmp.alloc(&ka, (size_t)m * key_bytes, "query keys");
-            if (st == KNN_OK) st = tmp.alloc(&kb, (size_t)m * key_bytes, "query keys");
+            st = tmp.alloc(&ka, (size_t)m, "query keys");
+            if (st == KNN_OK) st = tmp.alloc(&kb, (size_t)m, "query keys");
             if (st == KNN_OK) st = tmp.alloc(&va, (size_t)m, "query order");
             if (st == KNN_OK) st = tmp.alloc(&vb, (size_t)m, "query order");
             if (st == KNN_OK) st = tmp.alloc(&rtmp, radix_temp_bytes(m), "sort temp");
             if (st != KNN_OK) return st;
-            unsigned int* sv;
-            if (narrow) {
-                auto k32a = reinterpret_cast<unsigned int*>(ka), k32b = reinterpret_cast<unsigned int*>(kb);
-                unsigned int* sk;
-                GHN_CHECK(launch_query_keys(q, m, x->g, k32a, s), "query keys");
-                GHN_CHECK(radix_sort_pairs(k32a, va, k32b, vb, m, x->key_bits, rtmp, &sk, &sv, s,
-                                           true),
-                          "query order");
-            } else {
-                auto k64a = reinterpret_cast<unsigned long long*>(ka);
-                auto k64b = reinterpret_cast<unsigned long long*>(kb);
-                unsigned long long* sk;
-                GHN_CHECK(launch_query_keys(q, m, x->g, k64a, s), "query keys");
-                GHN_CHECK(radix_sort_pairs(k64a, va, k64b, vb, m, x->key_bits, rtmp, &sk, &sv, s,
-                                           true),
-                          "query order");
-            }
+            unsigned int *sk, *sv;
+            GHN_CHECK(launch_query_keys(q, m, x->g, shift, ka, s), "query keys");
+            GHN_CHECK(radix_sort_pairs(ka, va, kb, vb, m, x->key_bits - shift, rtmp, &sk, &sv, s,
+                                       true),
+                      "query order");
             order = sv;
         }
 

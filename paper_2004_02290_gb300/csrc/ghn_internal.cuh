@@ -222,10 +222,9 @@ cudaError_t launch_query_d34(const QueryArgs& a, int sms, cudaStream_t s);
 cudaError_t launch_query_d56(const QueryArgs& a, int sms, cudaStream_t s);
 cudaError_t launch_query_d78(const QueryArgs& a, int sms, cudaStream_t s);
 
-// Query keys for the locality order (cell id of each query, clamped into the box).
-cudaError_t launch_query_keys(const float* q, long long m, const GridConst& g,
-                              unsigned long long* keys, cudaStream_t s);
-cudaError_t launch_query_keys(const float* q, long long m, const GridConst& g, unsigned int* keys,
-                              cudaStream_t s);
+// Query keys for the locality order: the cell id of each query, clamped into
+// the box, shifted right by `shift` bits (the caller keeps it below 2^32).
+cudaError_t launch_query_keys(const float* q, long long m, const GridConst& g, int shift,
+                              unsigned int* keys, cudaStream_t s);
 
 }  // namespace ghn

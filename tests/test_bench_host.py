@@ -99,6 +99,16 @@ def test_committed_summaries_match_their_names():
             assert wk.group(1) == name, path
 
 
+def test_query_order_per_workload():
+    class K:
+        KNN_QUERY_SORTED = 2
+    assert bench.query_order("skewed_reg") == "cell"
+    assert bench.query_order("large_cls") == "input"
+    assert bench.query_flags(K, "skewed_reg") == 2 and bench.query_flags(K, "large_cls") == 0
+    assert bench.query_flags(K, "skewed_reg", "input") == 0
+    assert bench.query_flags(K, "large_cls", "cell") == 2
+
+
 def test_reference_arm_prints_one_line():
     r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--config", "tiny",
                         "--steps", "2", "--warmup", "1"], cwd=ROOT, capture_output=True,

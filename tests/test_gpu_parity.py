@@ -435,7 +435,7 @@ def _sampled_full(name, sample, flags):
 def test_full_large_cls_sampled():
     import bench
 
-    _sampled_full("large_cls", 3000, bench.QUERY_FLAGS)
+    _sampled_full("large_cls", 3000, bench.query_flags(knn, "large_cls"))
 
 
 def test_full_large_cls_sampled_sorted():
@@ -445,7 +445,11 @@ def test_full_large_cls_sampled_sorted():
 def test_full_skewed_reg_sampled():
     import bench
 
-    _sampled_full("skewed_reg", 1500, bench.QUERY_FLAGS)
+    _sampled_full("skewed_reg", 1500, bench.query_flags(knn, "skewed_reg"))
+
+
+def test_full_skewed_reg_sampled_input_order():
+    _sampled_full("skewed_reg", 800, 0)
 
 
 def test_full_large_cls_sampled_certified_stop():
