@@ -112,6 +112,9 @@ typedef struct {
  * 2^31 - 1 cells along one dimension, more than 2^63 cells in the box, or a
  * dense table of more than 2^31 entries; KNN_ENOMEM; KNN_ECUDA.
  * The call synchronizes `stream` once, to read the box of occupied cells.
+ * Host inputs are copied to the device; labels in pinned host memory are
+ * copied on a library-owned side stream while the build runs, and the build
+ * waits for that copy before it returns.
  */
 knn_status knn_build(const float* points, const void* labels, int64_t n, int32_t d,
                      float cell_width, int32_t table, void* stream, ghn_index** out);
@@ -164,7 +167,9 @@ knn_status knn_index_grid(const ghn_index* index, float* cell_widths, int64_t* s
  *   flags    KNN_QUERY_CHECKED | KNN_QUERY_SORTED | KNN_QUERY_EXACT.
  *   stream   cudaStream_t or NULL.
  * Device outputs are written asynchronously on `stream`; host outputs are
- * filled before the call returns.  A query with a non-finite coordinate gets
+ * filled before the call returns.  Pinned host outputs (page-locked memory the
+ * GPU can address, e.g. over NVLink-C2C) are written by the kernels directly;
+ * other host outputs are staged in device memory and copied out.  A query with a non-finite coordinate gets
  * -1 / +inf rows (KNN_EINVAL under KNN_QUERY_CHECKED); a query that reaches
  * the layer cap set by the GHN_MAX_LAYERS environment variable (0 or unset:
  * no cap) gets -1 / +inf rows (KNN_ELIMIT under KNN_QUERY_CHECKED).

@@ -249,6 +249,42 @@ knn_status device_view(const T* user, size_t count, bool in, Temps& tmp, T** out
     return KNN_OK;
 }
 
+// An output buffer as the kernels see it.  Device memory is used as is.
+// Pinned host memory that the GPU can address (NVLink-C2C on GB300, mapped
+// memory elsewhere) is written by the kernels directly, so the results cross
+// to the host while the search runs.  Any other host memory gets a temporary
+// that is copied out after the kernels.
+template <class T>
+struct OutView {
+    T* dev = nullptr;     // what the kernels write
+    bool staged = false;  // dev is a temporary: copy it to the caller's buffer
+    bool host = false;    // the caller's buffer is host memory: synchronize before returning
+};
+
+template <class T>
+knn_status output_view(T* user, size_t count, Temps& tmp, OutView<T>* v, const char* what)
+{
+    *v = OutView<T>{};
+    if (!user) return KNN_OK;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, user) != cudaSuccess) {
+        cudaGetLastError();
+        at.type = cudaMemoryTypeUnregistered;
+        at.devicePointer = nullptr;
+    }
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+        v->dev = user;
+        return KNN_OK;
+    }
+    v->host = true;
+    if (at.type == cudaMemoryTypeHost && at.devicePointer) {
+        v->dev = static_cast<T*>(at.devicePointer);
+        return KNN_OK;
+    }
+    v->staged = true;
+    return tmp.alloc(&v->dev, count, what);
+}
+
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev)
@@ -271,6 +307,31 @@ int num_sms(int dev)
     if (v <= 0) v = 1;
     if (dev >= 0 && dev < 64) cache[dev] = v;
     return v;
+}
+
+// A non-blocking stream per device for copies that overlap a build (created
+// on first use, kept for the life of the process), or null.
+cudaStream_t side_stream(int dev)
+{
+    static std::mutex mu;
+    static cudaStream_t streams[64] = {};
+    if (dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        streams[dev] = nullptr;
+    }
+    return streams[dev];
+}
+
+bool pinned_host(const void* p)
+{
+    cudaPointerAttributes at;
+    if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeHost;
 }
 
 void free_index(ghn_index* x)
@@ -297,9 +358,16 @@ knn_status build_impl(const float* points_user, const void* labels_user, long lo
     GHN_CHECK(cudaGetDevice(&dev), "cudaGetDevice");
     tune_pool(dev);
     ghn_index* x = new ghn_index();
-    // on failure: wait for the work already queued on the stream, then release
+    cudaEvent_t lab_done = nullptr;  // the side-stream copy of pinned host labels
+    // on failure: wait for the work already queued (on the stream and the
+    // side stream), then release
     auto fail = [&](knn_status code) {
         cudaStreamSynchronize(s);
+        if (lab_done) {
+            cudaEventSynchronize(lab_done);
+            cudaEventDestroy(lab_done);
+            lab_done = nullptr;
+        }
         cudaGetLastError();
         free_index(x);
         return code;
@@ -316,12 +384,42 @@ knn_status build_impl(const float* points_user, const void* labels_user, long lo
         float* pts_dev = nullptr;
         st = device_view(points_user, (size_t)(n * d), true, tmp, &pts_dev, "points");
         pts = pts_dev;
+        // labels: a caller's device buffer is copied into the index at the
+        // end; pinned host labels go straight into the index on a side stream,
+        // overlapping the build (joined before the build returns); other
+        // host labels are staged first
         const unsigned int* lab_in = nullptr;
         if (st == KNN_OK && labels_user) {
-            unsigned int* lv = nullptr;
-            st = device_view(static_cast<const unsigned int*>(labels_user), (size_t)n, true, tmp,
-                             &lv, "labels");
-            lab_in = lv;
+            const auto* lu = static_cast<const unsigned int*>(labels_user);
+            cudaStream_t side = pinned_host(lu) ? side_stream(dev) : nullptr;
+            cudaEvent_t ready = nullptr;
+            if (side && dalloc(&x->labels, (size_t)n, s, "labels") == KNN_OK &&
+                cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) == cudaSuccess &&
+                cudaEventCreateWithFlags(&lab_done, cudaEventDisableTiming) == cudaSuccess &&
+                cudaEventRecord(ready, s) == cudaSuccess &&
+                cudaStreamWaitEvent(side, ready, 0) == cudaSuccess &&
+                cudaMemcpyAsync(x->labels, lu, (size_t)n * 4, cudaMemcpyHostToDevice, side) ==
+                    cudaSuccess &&
+                cudaEventRecord(lab_done, side) == cudaSuccess) {
+                cudaEventDestroy(ready);
+            } else {
+                cudaGetLastError();
+                if (ready) cudaEventDestroy(ready);
+                if (lab_done) {
+                    // a copy may have been queued: wait for the side stream
+                    // before the labels buffer is used or freed
+                    if (side) cudaStreamSynchronize(side);
+                    cudaEventDestroy(lab_done);
+                    lab_done = nullptr;
+                }
+                if (x->labels) {
+                    dfree(x->labels, s);
+                    x->labels = nullptr;
+                }
+                unsigned int* lv = nullptr;
+                st = device_view(lu, (size_t)n, true, tmp, &lv, "labels");
+                lab_in = lv;
+            }
         }
         g_timer.mark("stage", s);
         // ---- box of the training points and cells per dimension (one sync) ----
@@ -496,6 +594,11 @@ knn_status build_impl(const float* points_user, const void* labels_user, long lo
         e = launch_gather(pts, n, d, x->rid, x->rows, s);
         if (e == cudaSuccess && lab_in)
             e = cudaMemcpyAsync(x->labels, lab_in, (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
+        if (lab_done) {
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, lab_done, 0);
+            cudaEventDestroy(lab_done);
+            lab_done = nullptr;
+        }
         g_timer.mark("gather", s);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x->last_use, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventRecord(x->last_use, s);
@@ -520,20 +623,22 @@ knn_status query_impl(const ghn_index* x, const float* queries_user, long long m
     {
         Temps tmp(s);
         float* q = nullptr;
-        int* ids = nullptr;
-        float* dist2 = nullptr;
-        unsigned int* pred = nullptr;
-        long long* stats = nullptr;
+        OutView<int> v_ids;
+        OutView<float> v_d2;
+        OutView<unsigned int> v_pred;
+        OutView<long long> v_stats;
         st = device_view(queries_user, (size_t)(m * d), true, tmp, &q, "queries");
-        if (st == KNN_OK) st = device_view(ids_user, (size_t)(m * k), false, tmp, &ids, "ids");
-        if (st == KNN_OK) st = device_view(dist2_user, (size_t)(m * k), false, tmp, &dist2, "dist2");
+        if (st == KNN_OK) st = output_view(ids_user, (size_t)(m * k), tmp, &v_ids, "ids");
+        if (st == KNN_OK) st = output_view(dist2_user, (size_t)(m * k), tmp, &v_d2, "dist2");
         if (st == KNN_OK && mode >= 0)
-            st = device_view(static_cast<unsigned int*>(pred_user), (size_t)m, false, tmp, &pred, "pred");
-        if (st == KNN_OK) st = device_view(stats_user, (size_t)(m * 3), false, tmp, &stats, "stats");
+            st = output_view(static_cast<unsigned int*>(pred_user), (size_t)m, tmp, &v_pred, "pred");
+        if (st == KNN_OK) st = output_view(stats_user, (size_t)(m * 3), tmp, &v_stats, "stats");
         if (st != KNN_OK) return st;
-        host_out = ids != ids_user || (dist2_user && dist2 != dist2_user) ||
-                   (mode >= 0 && pred_user && (void*)pred != pred_user) ||
-                   (stats_user && stats != stats_user);
+        int* ids = v_ids.dev;
+        float* dist2 = v_d2.dev;
+        unsigned int* pred = v_pred.dev;
+        long long* stats = v_stats.dev;
+        host_out = v_ids.host || v_d2.host || v_pred.host || v_stats.host;
 
         g_timer.mark("stage", s);
         // scratch: work counter, status word, deferral counters, deferred list
@@ -602,13 +707,13 @@ knn_status query_impl(const ghn_index* x, const float* queries_user, long long m
         GHN_CHECK(launch_query(a, num_sms(x->device), s), "query kernel");
         g_timer.mark("search", s);
 
-        if (ids != ids_user)
+        if (v_ids.staged)
             GHN_CHECK(cudaMemcpyAsync(ids_user, ids, (size_t)(m * k) * 4, cudaMemcpyDeviceToHost, s), "ids");
-        if (dist2_user && dist2 != dist2_user)
+        if (v_d2.staged)
             GHN_CHECK(cudaMemcpyAsync(dist2_user, dist2, (size_t)(m * k) * 4, cudaMemcpyDeviceToHost, s), "dist2");
-        if (mode >= 0 && pred_user && (void*)pred != pred_user)
+        if (v_pred.staged)
             GHN_CHECK(cudaMemcpyAsync(pred_user, pred, (size_t)m * 4, cudaMemcpyDeviceToHost, s), "pred");
-        if (stats_user && stats != stats_user)
+        if (v_stats.staged)
             GHN_CHECK(cudaMemcpyAsync(stats_user, stats, (size_t)(m * 3) * 8, cudaMemcpyDeviceToHost, s), "stats");
         if ((flags & KNN_QUERY_CHECKED) || stats_user)
             GHN_CHECK(cudaMemcpyAsync(&status_host, scratch + 1, 4, cudaMemcpyDeviceToHost, s), "status");

@@ -301,6 +301,34 @@ def test_host_buffers_match_device_buffers():
     idx.free()
 
 
+@pytest.mark.parametrize("mode", [knn.KNN_VOTE, knn.KNN_MEAN])
+def test_pinned_host_buffers(mode):
+    """Pinned host inputs and outputs: the labels are copied into the index on a
+    side stream during the build, and the kernels write ids, distances and
+    predictions straight into the pinned outputs.  Pageable outputs (numpy)
+    and device outputs give the same bytes."""
+    w = wl.make("large_cls", n=60_000, m=4_000, w=0.04)
+    lab = w.labels if mode == knn.KNN_VOTE else w.labels.astype(np.float32) * 0.5
+    pts_h = torch.from_numpy(w.points).pin_memory()
+    lab_h = torch.from_numpy(lab).pin_memory()
+    q_h = torch.from_numpy(w.queries).pin_memory()
+    idx = knn.knn_build(pts_h, lab_h, w.w)
+    ids = torch.full((w.m, w.k), -7, dtype=torch.int32).pin_memory()
+    d2 = torch.full((w.m, w.k), -7.0, dtype=torch.float32).pin_memory()
+    pred = torch.full((w.m,), -7, dtype=torch.int32 if mode == knn.KNN_VOTE else torch.float32)
+    pred = pred.pin_memory()
+    knn.knn_query(idx, q_h, w.k, mode, flags=knn.KNN_QUERY_CHECKED, ids=ids, dist2=d2, pred=pred)
+    got = (ids.numpy(), d2.numpy(), pred.numpy())  # filled when the call returns
+    assert_same(got, oracle_run(w.points, lab, w.queries, w.w, w.k, mode), mode)
+    pg = idx.query(w.queries, w.k, mode)  # pageable host outputs (staged copies)
+    dv = idx.query(_dev(w.queries), w.k, mode)  # device outputs
+    torch.cuda.synchronize()
+    for a, b_, c in zip(got, pg, dv):
+        assert np.array_equal(a.view(np.uint32), np.asarray(b_).view(np.uint32))
+        assert np.array_equal(a.view(np.uint32), c.cpu().numpy().view(np.uint32))
+    idx.free()
+
+
 def test_empty_query_batch():
     w = wl.make("tiny")
     idx = knn.knn_build(_dev(w.points), _dev(w.labels), w.w)
