@@ -21,7 +21,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["capi.cu", "build_kernels.cu", "query_d12.cu", "query_d34.cu", "query_d56.cu",
            "query_d78.cu", "noalloc.cu", "batch.cu", "serve.cu",
            "measure.cu"]
-HEADERS = ["ghn_internal.cuh", "query_kernel.cuh"]
+HEADERS = ["ghn_internal.cuh", "build_launch.cuh", "query_kernel.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-prec-div=true", "-prec-sqrt=true",

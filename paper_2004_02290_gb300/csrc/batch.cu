@@ -15,6 +15,7 @@
 //   - queries of all indexes with the same dimension run in one persistent
 //     launch; a plan captures those launches in a CUDA graph for replay.
 
+#include "build_launch.cuh"
 #include "ghn_internal.cuh"
 #include "../../include/ghn_knn.h"
 

@@ -11,6 +11,7 @@
 // Every kernel is a streaming pass bound by HBM bandwidth; none is a dense
 // contraction, so tensor cores have no role here.
 
+#include "build_launch.cuh"
 #include "ghn_internal.cuh"
 
 #include <math.h>

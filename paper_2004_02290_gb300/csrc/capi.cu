@@ -3,6 +3,7 @@
 // stream.  The entry points are declared, with their contracts, in
 // include/ghn_knn.h.
 
+#include "build_launch.cuh"
 #include "ghn_internal.cuh"
 #include "../../include/ghn_knn.h"
 

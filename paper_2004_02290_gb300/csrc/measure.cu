@@ -26,6 +26,7 @@
 #include <algorithm>
 
 #include "../../include/ghn_knn.h"
+#include "build_launch.cuh"
 #include "ghn_internal.cuh"
 
 using namespace ghn;

@@ -235,13 +235,18 @@ def test_cell_id_width_boundary(hi0, space, flags):
 
 @pytest.mark.parametrize("d,n", [(3, 4001), (5, 4003), (2, 3), (4, 4096)])
 @pytest.mark.parametrize("offset", [0, 1])
-def test_point_alignment_and_tails(d, n, offset):
+@pytest.mark.parametrize("where", ["device", "pinned"])
+def test_point_alignment_and_tails(d, n, offset, where):
     """Points at a 16-byte boundary (the box and keys kernels load 4 points a
     thread, the last n mod 4 one by one) and one float past it (the scalar
-    kernels)."""
+    kernels), in device memory or in pinned host memory (copied first)."""
     x, lab, q = wl.uniform(n, 200, d, seed=40 + d)
-    buf = torch.zeros(n * d + offset, dtype=torch.float32, device="cuda")
-    buf[offset:] = torch.from_numpy(x).cuda().reshape(-1)
+    if where == "device":
+        buf = torch.zeros(n * d + offset, dtype=torch.float32, device="cuda")
+        buf[offset:] = torch.from_numpy(x).cuda().reshape(-1)
+    else:
+        buf = torch.zeros(n * d + offset, dtype=torch.float32).pin_memory()
+        buf[offset:] = torch.from_numpy(x).reshape(-1)
     pts = buf[offset:].view(n, d)
     assert (pts.data_ptr() % 16 == 0) == (offset == 0)
     idx = knn.knn_build(pts, _dev(lab), 0.1)
