@@ -282,9 +282,12 @@ knn_status knn_index_export(const ghn_index* index, uint64_t* cell_keys, uint32_
  * Phase timing, for profiling.  While enabled, knn_build and knn_query record
  * a CUDA event on the call's stream at each phase boundary (build: stage, box,
  * keys, sort, cells, table, gather; query: stage, order, search, copy).
- * knn_timing_read waits for the last call's events on the calling thread and
- * writes up to `cap` phase names (static strings) and device milliseconds;
- * it returns the number of phases.
+ * The calling thread keeps its last 64 calls; enabling clears them.
+ * knn_timing_read takes the calling thread's oldest unread call, waits for
+ * its events, and writes up to `cap` phase names (static strings) and device
+ * milliseconds; it returns the number of phases (0 when no call is unread).
+ * Reading after a sequence of calls, rather than between them, adds no
+ * synchronisation between the calls.
  */
 knn_status knn_timing_enable(int32_t on);
 int32_t knn_timing_read(const char** names, float* ms, int32_t cap);

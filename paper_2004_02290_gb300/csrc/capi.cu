@@ -122,35 +122,64 @@ long long max_layers_env()
 std::atomic<int> g_timing_on{0};
 std::atomic<long long> g_launches{0};
 
-struct PhaseTimer {
+// The phase events of one call.
+struct PhaseCall {
     static constexpr int kMax = 16;
     cudaEvent_t ev[kMax + 1] = {};
     const char* names[kMax] = {};
-    int count = 0;     // phases recorded by the last call
+    int count = 0;  // phases recorded
     int device = -1;
-    bool active = false;
 
+    void ensure(int dev)
+    {
+        if (device == dev) return;
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+        for (auto& e : ev) cudaEventCreate(&e);
+        device = dev;
+    }
+};
+
+// A ring of the calling thread's last calls, read oldest first, so that a
+// caller can read them after a whole sequence of calls, without a
+// synchronisation between the calls.
+struct PhaseTimer {
+    static constexpr int kRing = 64;
+    PhaseCall calls[kRing];
+    long long head = 0;  // calls begun
+    long long tail = 0;  // calls read (or dropped)
+    PhaseCall* cur = nullptr;
+
+    void reset()
+    {
+        tail = head;
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        for (auto& c : calls) c.ensure(dev);  // no event creation inside a timed loop
+    }
     void begin(cudaStream_t s)
     {
-        active = g_timing_on.load() != 0;
-        count = 0;
-        if (!active) return;
+        cur = nullptr;
+        if (g_timing_on.load() == 0) return;
+        if (head - tail == kRing) ++tail;  // the oldest unread call is dropped
+        PhaseCall& c = calls[head % kRing];
+        ++head;
         int dev = 0;
         cudaGetDevice(&dev);
-        if (device != dev) {
-            for (auto& e : ev)
-                if (e) cudaEventDestroy(e);
-            for (auto& e : ev) cudaEventCreate(&e);
-            device = dev;
-        }
-        cudaEventRecord(ev[0], s);
+        c.ensure(dev);
+        c.count = 0;
+        cudaEventRecord(c.ev[0], s);
+        cur = &c;
     }
     void mark(const char* name, cudaStream_t s)
     {
-        if (!active || count >= kMax) return;
-        names[count] = name;
-        cudaEventRecord(ev[count + 1], s);
-        ++count;
+        if (!cur || cur->count >= PhaseCall::kMax) return;
+        cur->names[cur->count] = name;
+        cudaEventRecord(cur->ev[cur->count + 1], s);
+        ++cur->count;
     }
 };
 
@@ -1089,27 +1118,31 @@ knn_status knn_index_export(const ghn_index* index, uint64_t* cell_keys, uint32_
 knn_status knn_timing_enable(int32_t on)
 {
     g_timing_on = on ? 1 : 0;
+    if (on) g_timer.reset();
     return KNN_OK;
 }
 
 int32_t knn_timing_read(const char** names, float* ms, int32_t cap)
 {
     PhaseTimer& t = g_timer;
-    if (!t.active || t.count == 0) return 0;
-    if (cudaEventSynchronize(t.ev[t.count]) != cudaSuccess) {
+    if (t.tail == t.head) return 0;
+    PhaseCall& c = t.calls[t.tail % PhaseTimer::kRing];
+    ++t.tail;
+    if (c.count == 0) return 0;
+    if (cudaEventSynchronize(c.ev[c.count]) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
-    const int n = t.count < cap ? t.count : cap;
+    const int n = c.count < cap ? c.count : cap;
     for (int i = 0; i < n; ++i) {
-        if (names) names[i] = t.names[i];
+        if (names) names[i] = c.names[i];
         if (ms) {
             float v = 0.0f;
-            cudaEventElapsedTime(&v, t.ev[i], t.ev[i + 1]);
+            cudaEventElapsedTime(&v, c.ev[i], c.ev[i + 1]);
             ms[i] = v;
         }
     }
-    return t.count;
+    return c.count;
 }
 
 int64_t knn_kernel_launches(void) { return g_launches.load(); }

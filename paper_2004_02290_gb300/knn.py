@@ -508,7 +508,8 @@ def knn_timing_enable(on: bool = True):
 
 
 def knn_timing_read() -> list[tuple[str, float]]:
-    """Phases of the last build / query on this thread: [(name, device ms)]."""
+    """Phases of this thread's oldest unread build / query (of its last 64, while
+    timing is on): [(name, device ms)], or [] when none is unread."""
     names = (ctypes.c_char_p * 16)()
     ms = (ctypes.c_float * 16)()
     cnt = library().knn_timing_read(names, ms, 16)

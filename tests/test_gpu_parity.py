@@ -334,6 +334,33 @@ def test_pinned_host_buffers(mode):
     idx.free()
 
 
+def test_phase_timing_reads_calls_oldest_first():
+    w = wl.make("tiny")
+    knn.knn_timing_enable(True)
+    try:
+        idx = knn.knn_build(_dev(w.points), _dev(w.labels), w.w)
+        idx.query(_dev(w.queries), w.k, knn.KNN_VOTE)
+        idx.query(_dev(w.queries), w.k, knn.KNN_VOTE, flags=knn.KNN_QUERY_SORTED)
+        build = knn.knn_timing_read()
+        q1 = knn.knn_timing_read()
+        q2 = knn.knn_timing_read()
+        assert [n for n, _ in build] == ["stage", "box", "keys", "sort", "cells", "table",
+                                         "gather"]
+        assert [n for n, _ in q1] == [n for n, _ in q2] == ["stage", "order", "search", "copy"]
+        assert all(t >= 0.0 for _, t in build + q1 + q2)
+        assert knn.knn_timing_read() == []
+        # the thread keeps its last 64 calls: the oldest unread ones are dropped
+        for _ in range(70):
+            idx.query(_dev(w.queries[:10]), 1)
+        got = 0
+        while knn.knn_timing_read():
+            got += 1
+        assert got == 64
+        idx.free()
+    finally:
+        knn.knn_timing_enable(False)
+
+
 def test_empty_query_batch():
     w = wl.make("tiny")
     idx = knn.knn_build(_dev(w.points), _dev(w.labels), w.w)
