@@ -156,7 +156,7 @@ knn_status knn_index_grid(const ghn_index* index, float* cell_widths, int64_t* s
  * knn_query: exploration and prediction (Sec. III.B, Algorithm 2; Sec. I).
  *   index    from knn_build.
  *   queries  host or device, m*d float32, row-major.
- *   m        m >= 0 (0 is a no-op).
+ *   m        0 <= m < 2^31 (0 is a no-op; KNN_EINVAL beyond).
  *   k        1 <= k <= 64.
  *   mode     KNN_NONE / KNN_VOTE / KNN_MEAN / KNN_MEDIAN (all but NONE need
  *            labels).
