@@ -52,7 +52,7 @@ extern "C" {
 #define KNN_EINVAL 1 /* bad argument or input outside what the index can hold */
 #define KNN_ENOMEM 2 /* device or host allocation failed */
 #define KNN_ECUDA 3  /* a CUDA call failed; knn_last_error() has its text */
-#define KNN_ELIMIT 4 /* a query reached the layer cap; its rows are -1 / +inf */
+#define KNN_ELIMIT 4 /* a query reached its work bound; its rows are -1 / +inf */
 #define KNN_ETIMEDOUT 5 /* a wait ended before the request completed (ghn_serve.h) */
 typedef int32_t knn_status;
 
@@ -169,10 +169,19 @@ knn_status knn_index_grid(const ghn_index* index, float* cell_widths, int64_t* s
  * Device outputs are written asynchronously on `stream`; host outputs are
  * filled before the call returns.  Pinned host outputs (page-locked memory the
  * GPU can address, e.g. over NVLink-C2C) are written by the kernels directly;
- * other host outputs are staged in device memory and copied out.  A query with a non-finite coordinate gets
- * -1 / +inf rows (KNN_EINVAL under KNN_QUERY_CHECKED); a query that reaches
- * the layer cap set by the GHN_MAX_LAYERS environment variable (0 or unset:
- * no cap) gets -1 / +inf rows (KNN_ELIMIT under KNN_QUERY_CHECKED).
+ * other host outputs are staged in device memory and copied out.  A query
+ * with a non-finite coordinate gets -1 / +inf rows (KNN_EINVAL under
+ * KNN_QUERY_CHECKED).
+ * Work bound: a query that would enumerate more than 2^22 cell rows over the
+ * layers it visits (the rows of cube(L) clipped to the box of occupied cells,
+ * summed over L) stops there with -1 / +inf rows (KNN_ELIMIT under
+ * KNN_QUERY_CHECKED).  Only grids far finer than the k-th neighbour distance
+ * reach it (their walks need hundreds of layers); it keeps such a call from
+ * running for minutes.  The environment variable GHN_MAX_ROWS replaces the
+ * bound (0 or negative: none), and GHN_MAX_LAYERS adds a cap on the layers
+ * visited from the first one that reaches the box (0 or unset: none).  The
+ * bound and the cap apply to every query entry point of this library (batches,
+ * the server and knn_query_noalloc included).
  */
 knn_status knn_query(const ghn_index* index, const float* queries, int64_t m, int32_t k,
                      int32_t mode, int32_t* ids, float* dist2, void* pred, int32_t flags,
@@ -225,9 +234,11 @@ typedef struct ghn_plan ghn_plan;   /* a captured batch query (CUDA graph) */
 
 /*
  * knn_batch_build: build `count` indexes (1 <= count <= 65536).
- *   points[i]      device, n[i]*d[i] float32, row-major.
- *   labels         NULL, or an array whose entry i is a device pointer to
- *                  n[i] 32-bit outputs, or NULL for index i.
+ *   points[i]      host or device, n[i]*d[i] float32, row-major.
+ *   labels         NULL, or an array whose entry i points to n[i] 32-bit
+ *                  outputs (host or device), or is NULL for index i.
+ *   Host inputs are copied into one device buffer on `stream` (pinned host
+ *   memory makes those copies asynchronous DMA transfers).
  *   n, d, cell_width, table   host arrays of count entries, as in knn_build
  *                  (table may be NULL: KNN_TABLE_AUTO for every index).
  * The total number of points must be below 2^31.  Errors as knn_build, and
@@ -242,9 +253,15 @@ knn_status knn_batch_info(const ghn_batch* batch, int32_t i, knn_index_info_t* i
 
 /*
  * knn_batch_query: query every index of the batch (host arrays of count
- * entries; every data pointer is device memory; m[i] may be 0; the sum of
- * the m[i] must be below 2^32).  Outputs of
- * index i as knn_query's.  flags: KNN_QUERY_CHECKED, KNN_QUERY_EXACT.
+ * entries; m[i] may be 0; the sum of the m[i] must be below 2^32).  Outputs
+ * of index i as knn_query's.  flags: KNN_QUERY_CHECKED, KNN_QUERY_EXACT.
+ * Data pointers are host or device memory, as for knn_query: host queries
+ * are copied into one device buffer; outputs in pinned host memory are
+ * written by the kernels directly, other host outputs are staged on the
+ * device and copied out; host outputs are complete when the call returns.
+ * With knn_timing_enable on, the call records its phases (stage, one per
+ * kernel group "query.d<d>.<k32|k64>.<dense|hash>", copy); knn_batch_build
+ * records stage, box, keys, sort, cells, table, gather.
  */
 knn_status knn_batch_query(const ghn_batch* batch, const float* const* queries, const int64_t* m,
                            const int32_t* k, const int32_t* mode, int32_t* const* ids,
@@ -252,7 +269,8 @@ knn_status knn_batch_query(const ghn_batch* batch, const float* const* queries, 
 
 /*
  * knn_batch_plan / knn_batch_run: the same query captured once in a CUDA
- * graph (the buffers are fixed at plan time) and replayed by each run.
+ * graph (the buffers are fixed at plan time and must be device memory) and
+ * replayed by each run.
  * A plan must be freed before its batch.  knn_batch_run flags:
  * KNN_QUERY_CHECKED (synchronize and return the status) or 0.
  */
@@ -281,8 +299,10 @@ knn_status knn_index_export(const ghn_index* index, uint64_t* cell_keys, uint32_
 /*
  * Phase timing, for profiling.  While enabled, knn_build and knn_query record
  * a CUDA event on the call's stream at each phase boundary (build: stage, box,
- * keys, sort, cells, table, gather; query: stage, order, search, copy).
- * The calling thread keeps its last 64 calls; enabling clears them.
+ * keys, sort, cells, table, gather; query: stage, order, search (the warp
+ * kernel), coop (the cooperative kernel, when it runs), copy).
+ * The calling thread keeps its last 32 calls (up to 40 phases each); enabling
+ * clears them.
  * knn_timing_read takes the calling thread's oldest unread call, waits for
  * its events, and writes up to `cap` phase names (static strings) and device
  * milliseconds; it returns the number of phases (0 when no call is unread).

@@ -115,7 +115,7 @@ knn_status knn_server_drop(ghn_server* server, int64_t index_id, int64_t* ticket
 /*
  * knn_server_submit: a query request (the arguments of knn_query; results as
  * knn_query's with KNN_QUERY_CHECKED: the ticket's status is KNN_EINVAL for
- * a non-finite query and KNN_ELIMIT for one that reached the layer cap).
+ * a non-finite query and KNN_ELIMIT for one that reached its work bound, as knn_query).
  *   flags    0 or KNN_QUERY_EXACT (the certified stop for this request).
  *   queries  host, m*d float32 of the index's d; borrowed until completion.
  *   ids      host, m*k int32; dist2 host m*k float32 or NULL; pred host m

@@ -25,6 +25,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 using namespace ghn;
@@ -324,6 +325,9 @@ int grid_blocks(long long work)
     return (int)b;
 }
 
+// Device memory of the current GPU (the batch's), or managed memory.  Memory
+// of another GPU is refused: the kernels would reach it as a peer address
+// with no peer access set up.
 bool is_device(const void* p)
 {
     cudaPointerAttributes at;
@@ -331,10 +335,65 @@ bool is_device(const void* p)
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    int cur = -1;
+    return at.type == cudaMemoryTypeDevice && cudaGetDevice(&cur) == cudaSuccess &&
+           at.device == cur;
 }
 
+// Where a caller buffer lives.
+enum { kOtherGpu = -1, kHostMem = 0, kDeviceMem = 1, kMappedHost = 2 };
+
+// kDeviceMem: device memory of the current GPU, or managed memory;
+// kMappedHost: pinned host memory the GPU addresses (NVLink-C2C on GB300),
+// with its device address in *dptr; kHostMem: other host memory; kOtherGpu:
+// device memory of another GPU (refused).
+int pointer_kind(const void* p, void** dptr)
+{
+    if (dptr) *dptr = nullptr;
+    if (!p) return kHostMem;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return kHostMem;
+    }
+    if (at.type == cudaMemoryTypeManaged) return kDeviceMem;
+    if (at.type == cudaMemoryTypeDevice) {
+        int cur = -1;
+        return cudaGetDevice(&cur) == cudaSuccess && at.device == cur ? kDeviceMem : kOtherGpu;
+    }
+    if (at.type == cudaMemoryTypeHost && at.devicePointer) {
+        if (dptr) *dptr = at.devicePointer;
+        return kMappedHost;
+    }
+    return kHostMem;
+}
+
+
 }  // namespace
+
+namespace ghn {
+
+// Phase names of the batched query kernels (static strings for the timer).
+const char* group_phase_name(int d, int ns, int dense, int exact, bool coop)
+{
+    static char names[kMaxD + 1][2][2][2][2][40];
+    static std::once_flag once;
+    std::call_once(once, [] {
+        for (int dd = 0; dd <= kMaxD; ++dd)
+            for (int a = 0; a < 2; ++a)
+                for (int b = 0; b < 2; ++b)
+                    for (int c = 0; c < 2; ++c)
+                        for (int h = 0; h < 2; ++h)
+                            snprintf(names[dd][a][b][c][h], sizeof(names[dd][a][b][c][h]),
+                                     "query.d%d.%s.%s%s%s", dd, a ? "k64" : "k32",
+                                     b ? "dense" : "hash", c ? ".exact" : "", h ? ".coop" : "");
+    });
+    if (d < 0 || d > kMaxD) d = 0;
+    return names[d][ns == 2 ? 1 : 0][dense ? 1 : 0][exact ? 1 : 0][coop ? 1 : 0];
+}
+
+}  // namespace ghn
 
 // ---------------------------------------------------------------------------
 // host side
@@ -455,8 +514,48 @@ knn_status batch_build_impl(int count, const float* const* points, const void* c
         return code;
     };
     knn_status st = KNN_OK;
+    phase_begin(s);
     {
         Scratch sc(s);
+        // ---- host inputs: copied into one device buffer (16-byte aligned slices) ----
+        std::vector<const float*> pdev(points, points + count);
+        std::vector<const void*> ldev(count, nullptr);
+        if (labels) ldev.assign(labels, labels + count);
+        {
+            const size_t none = ~(size_t)0;
+            std::vector<size_t> p_at(count, none), l_at(count, none);
+            size_t words = 0;
+            for (int i = 0; i < count; ++i) {
+                if (pointer_kind(points[i], nullptr) != kDeviceMem) {
+                    words = (words + 3) & ~(size_t)3;
+                    p_at[i] = words;
+                    words += (size_t)n[i] * (size_t)d[i];
+                }
+                if (ldev[i] && pointer_kind(ldev[i], nullptr) != kDeviceMem) {
+                    words = (words + 3) & ~(size_t)3;
+                    l_at[i] = words;
+                    words += (size_t)n[i];
+                }
+            }
+            if (words > 0) {
+                float* stage = nullptr;
+                if ((st = sc.alloc(&stage, words, "batch staged inputs")) != KNN_OK) return bail(st);
+                for (int i = 0; i < count && e == cudaSuccess; ++i) {
+                    if (p_at[i] != none) {
+                        e = cudaMemcpyAsync(stage + p_at[i], points[i],
+                                            (size_t)n[i] * (size_t)d[i] * 4, cudaMemcpyHostToDevice, s);
+                        pdev[i] = stage + p_at[i];
+                    }
+                    if (l_at[i] != none && e == cudaSuccess) {
+                        e = cudaMemcpyAsync(stage + l_at[i], ldev[i], (size_t)n[i] * 4,
+                                            cudaMemcpyHostToDevice, s);
+                        ldev[i] = stage + l_at[i];
+                    }
+                }
+                if (e != cudaSuccess) return bail(cuda_error(e, "batch staged inputs"));
+            }
+        }
+        phase_mark("stage", s);
         // ---- per-index descriptors and tiles ----
         std::vector<BuildDesc> desc(count);
         std::vector<Tile> tiles;
@@ -465,8 +564,8 @@ knn_status batch_build_impl(int count, const float* const* points, const void* c
         for (int i = 0; i < count; ++i) {
             BuildDesc& ds = desc[i];
             memset(&ds, 0, sizeof(ds));
-            ds.points = points[i];
-            ds.labels = labels ? static_cast<const unsigned int*>(labels[i]) : nullptr;
+            ds.points = pdev[i];
+            ds.labels = static_cast<const unsigned int*>(ldev[i]);
             ds.n = n[i];
             ds.d = d[i];
             ds.p = row_floats(d[i]);
@@ -520,6 +619,7 @@ knn_status batch_build_impl(int count, const float* const* points, const void* c
         e = cudaMemcpyAsync(box.data(), dbox, sizeof(BoxOut) * count, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return bail(cuda_error(e, "batch boxes"));
+        phase_mark("box", s);
 
         // ---- layouts ----
         int shift = 0;
@@ -637,10 +737,13 @@ knn_status batch_build_impl(int count, const float* const* points, const void* c
         b->gdev = static_cast<GridDev*>(gv);
         batch_keys_kernel<<<(unsigned)tiles.size(), 256, 0, s>>>(ddesc, dtiles, shift, ka, va);
         count_launches(1);
+        phase_mark("keys", s);
         e = radix_sort_pairs(ka, va, kb, vb, total, shift + ib, rtmp, &sk, &sv, s);
+        phase_mark("sort", s);
         if (e == cudaSuccess)
             e = launch_cells(sk, total, stmp, cell_key, cell_start, b->gdev, s);
         if (e != cudaSuccess) return bail(cuda_error(e, "batch sort"));
+        phase_mark("cells", s);
 
         // ---- tables ----
         if (dense_total > 0) {
@@ -685,6 +788,7 @@ knn_status batch_build_impl(int count, const float* const* points, const void* c
             count_launches(1);
         }
         if (e != cudaSuccess) return bail(cuda_error(e, "batch tables"));
+        phase_mark("table", s);
 
         // ---- rows, row ids, labels ----
         if ((st = device_alloc(&gv, sizeof(float) * rows_total, s, "batch rows")) != KNN_OK) return bail(st);
@@ -705,6 +809,7 @@ knn_status batch_build_impl(int count, const float* const* points, const void* c
             count_launches(1);
         }
         e = cudaGetLastError();
+        phase_mark("gather", s);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->last_use, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventRecord(b->last_use, s);
         if (e != cudaSuccess) return bail(cuda_error(e, "batch gather"));
@@ -726,6 +831,7 @@ knn_status batch_build_impl(int count, const float* const* points, const void* c
             a.key_prefix = (unsigned long long)i << shift;
             a.gdev = b->gdev;
             a.max_layers = max_layers_default();
+            a.max_rows = max_rows_default();
             a.heavy_rows = heavy_rows_default(ds.d);
             a.heavy_cands = heavy_cands_default();
         }
@@ -749,7 +855,8 @@ struct Layout {
 
 knn_status plan_layout(const ghn_batch* b, const float* const* queries, const int64_t* m,
                        const int32_t* k, const int32_t* mode, int32_t* const* ids,
-                       float* const* dist2, void* const* pred, Layout& lay)
+                       float* const* dist2, void* const* pred, Layout& lay,
+                       bool require_device = true)
 {
     for (int i = 0; i < b->count; ++i) {
         char msg[160];
@@ -764,11 +871,17 @@ knn_status plan_layout(const ghn_batch* b, const float* const* queries, const in
             set_error(msg);
             return KNN_EINVAL;
         }
-        if (m[i] > 0 && (!is_device(queries[i]) || !is_device(ids[i]) ||
-                         (dist2 && dist2[i] && !is_device(dist2[i])) ||
-                         (mode[i] >= 0 && (!pred || !is_device(pred[i]))))) {
+        if (m[i] > 0 && (!queries[i] || !ids[i] || (mode[i] >= 0 && (!pred || !pred[i])))) {
+            snprintf(msg, sizeof(msg), "knn_batch_query: index %d: NULL queries or outputs", i);
+            set_error(msg);
+            return KNN_EINVAL;
+        }
+        if (require_device && m[i] > 0 &&
+            (!is_device(queries[i]) || !is_device(ids[i]) ||
+             (dist2 && dist2[i] && !is_device(dist2[i])) ||
+             (mode[i] >= 0 && (!pred || !is_device(pred[i]))))) {
             snprintf(msg, sizeof(msg),
-                     "knn_batch_query: index %d: queries and outputs must be device memory", i);
+                     "knn_batch_query: index %d: queries and outputs must be device memory of the batch's GPU", i);
             set_error(msg);
             return KNN_EINVAL;
         }
@@ -868,14 +981,17 @@ knn_status make_plan(const ghn_batch* b, Layout& lay, cudaStream_t s, ghn_plan* 
     return KNN_OK;
 }
 
-// The launches of one batch query: clear the counters, then each group.
-cudaError_t launch_plan(const ghn_plan* p, cudaStream_t s)
+// The launches of one batch query: clear the counters, then each group
+// (each kernel marked for the phase timer when `timed`; never inside a capture).
+cudaError_t launch_plan(const ghn_plan* p, cudaStream_t s, bool timed = false)
 {
     cudaError_t e = cudaMemsetAsync(p->counters, 0, p->counter_bytes, s);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+    set_kernel_marks(timed);
     for (size_t g = 0; e == cudaSuccess && g < p->groups.size(); ++g)
         e = launch_batch_query(p->groups[g], sms, s);
+    set_kernel_marks(false);
     return e;
 }
 
@@ -899,7 +1015,7 @@ knn_status read_status(const ghn_plan* p, cudaStream_t s)
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_error(e, "batch status");
     if (st & kStatusNonFinite) return fail("knn_batch_query: a query coordinate is not finite", KNN_EINVAL);
-    if (st & kStatusLimit) return fail("knn_batch_query: a query reached the layer cap", KNN_ELIMIT);
+    if (st & kStatusLimit) return fail("knn_batch_query: a query reached its work bound (rows or layer cap)", KNN_ELIMIT);
     return KNN_OK;
 }
 
@@ -924,8 +1040,10 @@ knn_status knn_batch_build(int32_t count, const float* const* points, const void
             snprintf(msg, sizeof(msg), "knn_batch_build: index %d: bad n, d, width or table", i);
             return fail(msg, KNN_EINVAL);
         }
-        if (!is_device(points[i]) || (labels && labels[i] && !is_device(labels[i]))) {
-            snprintf(msg, sizeof(msg), "knn_batch_build: index %d: data must be device memory", i);
+        if (!points[i] || pointer_kind(points[i], nullptr) == kOtherGpu ||
+            (labels && labels[i] && pointer_kind(labels[i], nullptr) == kOtherGpu)) {
+            snprintf(msg, sizeof(msg),
+                     "knn_batch_build: index %d: points are NULL or on another GPU than the current one", i);
             return fail(msg, KNN_EINVAL);
         }
     }
@@ -954,21 +1072,121 @@ knn_status knn_batch_query(const ghn_batch* batch, const float* const* queries, 
     cudaGetDevice(&prev);
     if (prev != batch->device) cudaSetDevice(batch->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int count = batch->count;
+    phase_begin(s);
+    // Host buffers.  Queries in host memory are copied into one device
+    // buffer.  Outputs in pinned host memory that the GPU addresses are
+    // written by the kernels directly; other host outputs get device space
+    // and are copied out after the kernels.  Host outputs are complete when
+    // the call returns.
+    std::vector<const float*> qd(count, nullptr);
+    std::vector<int32_t*> idd(count, nullptr);
+    std::vector<float*> d2d(count, nullptr);
+    std::vector<void*> pd(count, nullptr);
+    struct Copy {
+        void* dst;
+        const void* src;
+        size_t bytes;
+    };
+    std::vector<Copy> out_copies;
+    void* stage = nullptr;
+    bool host_out = false;
+    knn_status st = KNN_OK;
+    {
+        const size_t none = ~(size_t)0;
+        std::vector<size_t> q_at(count, none), i_at(count, none), d_at(count, none),
+            p_at(count, none);
+        size_t words = 0;
+        auto take = [&words](size_t count_words) {
+            words = (words + 3) & ~(size_t)3;
+            const size_t at = words;
+            words += count_words;
+            return at;
+        };
+        for (int i = 0; i < count && st == KNN_OK; ++i) {
+            if (m[i] <= 0) continue;
+            if (m[i] >= (1ll << 31) || k[i] < 1 || k[i] > kMaxK) break;  // plan_layout reports it
+            const size_t mi = (size_t)m[i], ki = (size_t)k[i];
+            const size_t di = (size_t)batch->info[i].d;
+            void* dp = nullptr;
+            int kind = pointer_kind(queries[i], &dp);
+            if (kind == kOtherGpu) st = fail("knn_batch_query: a buffer is device memory of another GPU", KNN_EINVAL);
+            qd[i] = queries[i];
+            if (kind == kHostMem || kind == kMappedHost) q_at[i] = take(mi * di);
+            kind = pointer_kind(ids[i], &dp);
+            if (kind == kOtherGpu) st = fail("knn_batch_query: a buffer is device memory of another GPU", KNN_EINVAL);
+            idd[i] = kind == kMappedHost ? static_cast<int32_t*>(dp) : ids[i];
+            if (kind == kHostMem) i_at[i] = take(mi * ki);
+            host_out |= kind == kHostMem || kind == kMappedHost;
+            if (dist2 && dist2[i]) {
+                kind = pointer_kind(dist2[i], &dp);
+                if (kind == kOtherGpu) st = fail("knn_batch_query: a buffer is device memory of another GPU", KNN_EINVAL);
+                d2d[i] = kind == kMappedHost ? static_cast<float*>(dp) : dist2[i];
+                if (kind == kHostMem) d_at[i] = take(mi * ki);
+                host_out |= kind == kHostMem || kind == kMappedHost;
+            }
+            if (pred && pred[i] && mode[i] >= 0) {
+                kind = pointer_kind(pred[i], &dp);
+                if (kind == kOtherGpu) st = fail("knn_batch_query: a buffer is device memory of another GPU", KNN_EINVAL);
+                pd[i] = kind == kMappedHost ? dp : pred[i];
+                if (kind == kHostMem) p_at[i] = take(mi);
+                host_out |= kind == kHostMem || kind == kMappedHost;
+            }
+        }
+        if (st == KNN_OK && words > 0) st = device_alloc(&stage, words * 4, s, "batch query staging");
+        cudaError_t e = cudaSuccess;
+        float* sw = static_cast<float*>(stage);
+        for (int i = 0; st == KNN_OK && i < count; ++i) {
+            if (m[i] <= 0) continue;
+            const size_t mi = (size_t)m[i], ki = (size_t)k[i];
+            const size_t di = (size_t)batch->info[i].d;
+            if (q_at[i] != none) {
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(sw + q_at[i], queries[i], mi * di * 4, cudaMemcpyHostToDevice, s);
+                qd[i] = sw + q_at[i];
+            }
+            if (i_at[i] != none) {
+                idd[i] = reinterpret_cast<int32_t*>(sw + i_at[i]);
+                out_copies.push_back(Copy{ids[i], idd[i], mi * ki * 4});
+            }
+            if (d_at[i] != none) {
+                d2d[i] = sw + d_at[i];
+                out_copies.push_back(Copy{dist2[i], d2d[i], mi * ki * 4});
+            }
+            if (p_at[i] != none) {
+                pd[i] = sw + p_at[i];
+                out_copies.push_back(Copy{pred[i], pd[i], mi * 4});
+            }
+        }
+        if (st == KNN_OK && e != cudaSuccess) st = cuda_error(e, "knn_batch_query: staging");
+    }
+    phase_mark("stage", s);
     Layout lay;
-    knn_status st = plan_layout(batch, queries, m, k, mode, ids, dist2, pred, lay);
+    if (st == KNN_OK)
+        st = plan_layout(batch, qd.data(), m, k, mode, idd.data(), dist2 ? d2d.data() : nullptr,
+                         pred ? pd.data() : nullptr, lay, false);
     for (QueryArgs& a : lay.args) a.exact = (flags & KNN_QUERY_EXACT) ? 1 : 0;
     ghn_plan p;
     p.device = batch->device;
     if (st == KNN_OK && !lay.args.empty()) {
         st = make_plan(batch, lay, s, &p);
         if (st == KNN_OK) {
-            cudaError_t e = launch_plan(&p, s);
+            cudaError_t e = launch_plan(&p, s, true);
+            for (size_t c = 0; e == cudaSuccess && c < out_copies.size(); ++c)
+                e = cudaMemcpyAsync(out_copies[c].dst, out_copies[c].src, out_copies[c].bytes,
+                                    cudaMemcpyDeviceToHost, s);
+            if (!out_copies.empty()) phase_mark("copy", s);
             if (e == cudaSuccess) e = cudaEventRecord(batch->last_use, s);
             if (e != cudaSuccess) st = cuda_error(e, "knn_batch_query");
             if (st == KNN_OK && (flags & KNN_QUERY_CHECKED)) st = read_status(&p, s);
         }
         if (p.dev_buf) device_free(p.dev_buf, s);
         p.dev_buf = nullptr;
+    }
+    if (stage) device_free(stage, s);
+    if (host_out) {
+        const cudaError_t e = cudaStreamSynchronize(s);
+        if (st == KNN_OK && e != cudaSuccess) st = cuda_error(e, "knn_batch_query: synchronize");
     }
     if (prev >= 0 && prev != batch->device) cudaSetDevice(prev);
     return st;

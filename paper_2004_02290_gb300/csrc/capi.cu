@@ -117,6 +117,27 @@ long long max_layers_env()
     return v;
 }
 
+// Default bound on a query's work: 2^22 cell rows enumerated over its layers
+// (the rows of cube(L) clipped to the box, summed over the layers visited).
+// A walk on a grid far finer than its k-th distance (e.g. a measured grid on
+// dense data) needs thousands of layers of (2L + 1)^(d - 1) rows each; this
+// bound ends such a query after a few hundred layers in d = 3, with -1 / +inf
+// rows and KNN_ELIMIT, so that one call cannot run for minutes.  The bench
+// and test workloads enumerate at most a few thousand rows per query.
+// GHN_MAX_ROWS overrides it (0 or a negative value: no bound).
+constexpr long long kDefaultMaxRows = 1ll << 22;
+
+long long max_rows_env()
+{
+    static long long v = [] {
+        const char* s = getenv("GHN_MAX_ROWS");
+        if (!s || !*s) return kDefaultMaxRows;
+        const long long x = atoll(s);
+        return x > 0 ? x : 0ll;
+    }();
+    return v;
+}
+
 // ---- phase timing (knn_timing_enable / knn_timing_read) ----
 
 std::atomic<int> g_timing_on{0};
@@ -124,7 +145,7 @@ std::atomic<long long> g_launches{0};
 
 // The phase events of one call.
 struct PhaseCall {
-    static constexpr int kMax = 16;
+    static constexpr int kMax = 40;
     cudaEvent_t ev[kMax + 1] = {};
     const char* names[kMax] = {};
     int count = 0;  // phases recorded
@@ -144,7 +165,7 @@ struct PhaseCall {
 // caller can read them after a whole sequence of calls, without a
 // synchronisation between the calls.
 struct PhaseTimer {
-    static constexpr int kRing = 64;
+    static constexpr int kRing = 32;
     PhaseCall calls[kRing];
     long long head = 0;  // calls begun
     long long tail = 0;  // calls read (or dropped)
@@ -247,15 +268,29 @@ struct Temps {
     }
 };
 
-bool is_device_ptr(const void* p)
+// Where a caller buffer lives: 1 device memory of the current GPU (or managed
+// memory), 0 host memory, -1 device memory of another GPU.  The kernels would
+// reach another GPU's memory as a peer address with no peer access set up, so
+// such buffers are refused.
+int pointer_kind(const void* p)
 {
-    if (!p) return false;
+    if (!p) return 0;
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return 0;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return 1;
+    if (at.type != cudaMemoryTypeDevice) return 0;
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return -1;
+    return at.device == cur ? 1 : -1;
+}
+
+knn_status other_gpu(const char* what)
+{
+    set_err("%s: device memory of another GPU than the index's", what);
+    return KNN_EINVAL;
 }
 
 // Device view of a caller buffer: the pointer itself when it is device memory,
@@ -268,7 +303,9 @@ knn_status device_view(const T* user, size_t count, bool in, Temps& tmp, T** out
         *out = nullptr;
         return KNN_OK;
     }
-    if (is_device_ptr(user)) {
+    const int kind = pointer_kind(user);
+    if (kind < 0) return other_gpu(what);
+    if (kind > 0) {
         *out = const_cast<T*>(user);
         return KNN_OK;
     }
@@ -302,7 +339,13 @@ knn_status output_view(T* user, size_t count, Temps& tmp, OutView<T>* v, const c
         at.type = cudaMemoryTypeUnregistered;
         at.devicePointer = nullptr;
     }
-    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+    if (at.type == cudaMemoryTypeManaged) {
+        v->dev = user;
+        return KNN_OK;
+    }
+    if (at.type == cudaMemoryTypeDevice) {
+        int cur = -1;
+        if (cudaGetDevice(&cur) != cudaSuccess || at.device != cur) return other_gpu(what);
         v->dev = user;
         return KNN_OK;
     }
@@ -732,10 +775,14 @@ knn_status query_impl(const ghn_index* x, const float* queries_user, long long m
         a.stats = stats;
         a.order = order;
         a.max_layers = max_layers_env();
+        a.max_rows = max_rows_env();
         a.dense = x->table == KNN_TABLE_DENSE;
         a.exact = (flags & KNN_QUERY_EXACT) ? 1 : 0;
-        GHN_CHECK(launch_query(a, num_sms(x->device), s), "query kernel");
-        g_timer.mark("search", s);
+        // the launcher marks "search" (warp kernel) and "coop" (cooperative kernel)
+        set_kernel_marks(true);
+        const cudaError_t le = launch_query(a, num_sms(x->device), s);
+        set_kernel_marks(false);
+        GHN_CHECK(le, "query kernel");
 
         if (v_ids.staged)
             GHN_CHECK(cudaMemcpyAsync(ids_user, ids, (size_t)(m * k) * 4, cudaMemcpyDeviceToHost, s), "ids");
@@ -758,7 +805,7 @@ knn_status query_impl(const ghn_index* x, const float* queries_user, long long m
             return KNN_EINVAL;
         }
         if (status_host & kStatusLimit) {
-            set_err("knn_query: a query reached the layer cap");
+            set_err("knn_query: a query reached its work bound (rows or layer cap)");
             return KNN_ELIMIT;
         }
     }
@@ -805,6 +852,16 @@ namespace ghn {
 
 void count_launches(long long k) { g_launches += k; }
 
+void phase_begin(cudaStream_t s) { g_timer.begin(s); }
+void phase_mark(const char* name, cudaStream_t s) { g_timer.mark(name, s); }
+
+thread_local bool g_kernel_marks = false;
+void set_kernel_marks(bool on) { g_kernel_marks = on; }
+void kernel_mark(const char* name, cudaStream_t s)
+{
+    if (g_kernel_marks) g_timer.mark(name, s);
+}
+
 // Accessors for entry points defined in other translation units.
 void set_error(const char* msg) { set_err("%s", msg); }
 
@@ -827,6 +884,7 @@ void index_query_args(const ghn_index* x, QueryArgs& a)
     a.bitmap = x->bitmap;
     a.gdev = x->gdev;
     a.max_layers = max_layers_env();
+    a.max_rows = max_rows_env();
     a.heavy_rows = heavy_rows_env(x->d);
     a.heavy_cands = heavy_cands_env();
     a.dense = x->table == KNN_TABLE_DENSE;
@@ -869,6 +927,7 @@ void device_free(void* p, cudaStream_t s)
 unsigned int heavy_rows_default(int d) { return heavy_rows_env(d); }
 unsigned int heavy_cands_default() { return heavy_cands_env(); }
 long long max_layers_default() { return max_layers_env(); }
+long long max_rows_default() { return max_rows_env(); }
 void tune_device_pool(int dev) { tune_pool(dev); }
 
 cudaError_t launch_query(const QueryArgs& a, int sms, cudaStream_t s)

@@ -13,7 +13,7 @@ constexpr float kQueryClamp = 1099511627776.0f;  // 2^40
 
 // Status bits a kernel ORs into a device word.
 constexpr unsigned int kStatusNonFinite = 1u;  // a non-finite point or query
-constexpr unsigned int kStatusLimit = 2u;      // a query reached the layer cap
+constexpr unsigned int kStatusLimit = 2u;      // a query reached its work bound
 constexpr unsigned int kStatusExtent = 4u;     // too many cells along one dimension
 
 // Grid geometry, passed by value to the kernels.
@@ -70,6 +70,18 @@ __host__ __device__ constexpr int row_floats(int d) { return d <= 2 ? 2 : (d <= 
 // Count of kernels launched by this library (read by knn_kernel_launches).
 void count_launches(long long k);
 
+// Phase timing of knn_timing_enable: a call begins, then marks the end of
+// each phase with a static name (no effect while timing is off).
+void phase_begin(cudaStream_t s);
+void phase_mark(const char* name, cudaStream_t s);
+// While set on the calling thread, the query launchers mark the end of each
+// kernel they launch (knn_query, and knn_batch_query outside a graph capture).
+void set_kernel_marks(bool on);
+void kernel_mark(const char* name, cudaStream_t s);
+// Phase name of a batched query group's warp kernel, or of its cooperative
+// kernel (`coop`): "query.d<d>.<k32|k64>.<dense|hash>[.exact][.coop]".
+const char* group_phase_name(int d, int ns, int dense, int exact, bool coop);
+
 // ---- query ----
 struct QueryArgs {
     GridConst g;
@@ -98,6 +110,7 @@ struct QueryArgs {
     long long* stats;               // m*3 or null (exhaustive counting walk)
     const unsigned int* order;      // visiting order of queries or null
     long long max_layers;           // 0 = no cap
+    long long max_rows;             // cap on the cell rows a query enumerates, over its layers (0 = none)
     int dense;
     int exact;                      // certified stop instead of the paper's rule
 };
@@ -151,6 +164,7 @@ void device_free(void* p, cudaStream_t s);
 unsigned int heavy_rows_default(int d);
 unsigned int heavy_cands_default();
 long long max_layers_default();
+long long max_rows_default();
 void tune_device_pool(int dev);
 
 // Persistent launch: as many blocks as fit on `sms` SMs (fewer when m is small).

@@ -58,14 +58,17 @@ knn_status scratch_for(int dev, unsigned char** out)
     return KNN_OK;
 }
 
-bool on_device(const void* p)
+// Device memory of GPU `dev` (managed memory is reachable from every GPU).
+// Memory of another GPU is refused: the kernels would reach it as a peer
+// address, with no peer access set up.
+bool on_device(const void* p, int dev)
 {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    return at.type == cudaMemoryTypeManaged || (at.type == cudaMemoryTypeDevice && at.device == dev);
 }
 
 }  // namespace
@@ -107,10 +110,10 @@ extern "C" knn_status knn_query_noalloc(const ghn_index* index, const float* que
     if (prev != dev) cudaSetDevice(dev);
     knn_status st = KNN_OK;
     do {
-        if (!on_device(queries) || !on_device(ids) || (dist2 && !on_device(dist2)) ||
-            (mode >= 0 && !on_device(pred))) {
-            ghn::set_error("knn_query_noalloc: every buffer must be device memory (host data "
-                           "would need a staging allocation)");
+        if (!on_device(queries, dev) || !on_device(ids, dev) || (dist2 && !on_device(dist2, dev)) ||
+            (mode >= 0 && !on_device(pred, dev))) {
+            ghn::set_error("knn_query_noalloc: every buffer must be device memory of the index's "
+                           "GPU (host data would need a staging allocation)");
             st = KNN_EINVAL;
             break;
         }
@@ -148,7 +151,7 @@ extern "C" knn_status knn_query_noalloc(const ghn_index* index, const float* que
                 ghn::set_error("knn_query_noalloc: a query coordinate is not finite");
                 st = KNN_EINVAL;
             } else if (e == cudaSuccess && (status & ghn::kStatusLimit)) {
-                ghn::set_error("knn_query_noalloc: a query reached the layer cap");
+                ghn::set_error("knn_query_noalloc: a query reached its work bound (rows or layer cap)");
                 st = KNN_ELIMIT;
             }
         }

@@ -794,6 +794,7 @@ __device__ __forceinline__ bool walk_query(const QueryArgs& a, long long qid, Wa
     tk.init(a.k);
     long long L = s.lmin;
     long long cells = 0, cands = 0;
+    unsigned long long rows_seen = 0ull;  // rows enumerated so far (the work bound)
     bool limited = !s.finite, deferred = false;
     if (!s.finite && lane == 0) atomicOr(a.status, kStatusNonFinite);
 
@@ -804,7 +805,9 @@ __device__ __forceinline__ bool walk_query(const QueryArgs& a, long long qid, Wa
         bool updated = false;
         if (!b.empty) {
             const unsigned long long nrows = layer_rows(b);
-            if (nrows >= (1ull << 32)) {
+            rows_seen += nrows;
+            if (nrows >= (1ull << 32) ||
+                (a.max_rows > 0 && rows_seen > (unsigned long long)a.max_rows)) {
                 limited = true;
                 if (lane == 0) atomicOr(a.status, kStatusLimit);
                 break;
@@ -991,6 +994,7 @@ __device__ __forceinline__ void coop_query(const QueryArgs& a, long long qid, Co
 
     TopK<NS> tk;
     long long L = s.lmin;
+    unsigned long long rows_seen = 0ull;  // rows enumerated so far (the work bound)
     bool limited = false;
     for (;;) {
         // the block's k-th key at the start of the layer, and an empty list
@@ -1002,7 +1006,9 @@ __device__ __forceinline__ void coop_query(const QueryArgs& a, long long qid, Co
         layer_box(a, s, L, gkth != kEmptyKey && kd0 < 1e30f, kd0, b);
         if (!b.empty) {
             const unsigned long long nrows = layer_rows(b);
-            if (nrows >= (1ull << 32)) {
+            rows_seen += nrows;
+            if (nrows >= (1ull << 32) ||
+                (a.max_rows > 0 && rows_seen > (unsigned long long)a.max_rows)) {
                 limited = true;
                 if (threadIdx.x == 0) atomicOr(a.status, kStatusLimit);
                 break;
@@ -1260,6 +1266,7 @@ cudaError_t launch_one(const QueryArgs& a, int sms, cudaStream_t s)
     if (blocks < 1) blocks = 1;
     query_kernel<D, NS, DENSE, EXACT, COUNT><<<(int)blocks, kThreads, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();
+    kernel_mark("search", s);
     if (e != cudaSuccess || a.heavy_list == nullptr || COUNT) return e;
     long long hb =
         (long long)sms * blocks_per_sm(heavy_kernel<D, NS, DENSE, EXACT>, per_sm_heavy);
@@ -1267,6 +1274,7 @@ cudaError_t launch_one(const QueryArgs& a, int sms, cudaStream_t s)
     if (hb < 1) hb = 1;
     heavy_kernel<D, NS, DENSE, EXACT><<<(int)hb, kThreads, 0, s>>>(a);
     count_launches(1);
+    kernel_mark("coop", s);
     return cudaGetLastError();
 }
 
@@ -1281,6 +1289,7 @@ cudaError_t launch_batch_one(const BatchArgs& g, int sms, cudaStream_t s)
     if (blocks < 1) blocks = 1;
     batch_query_kernel<D, NS, DENSE, EXACT><<<(int)blocks, kThreads, 0, s>>>(g);
     cudaError_t e = cudaGetLastError();
+    kernel_mark(group_phase_name(D, NS, DENSE, EXACT, false), s);
     if (e != cudaSuccess || g.heavy_list == nullptr) return e;
     long long hb =
         (long long)sms * blocks_per_sm(batch_heavy_kernel<D, NS, DENSE, EXACT>, per_sm_heavy);
@@ -1288,6 +1297,7 @@ cudaError_t launch_batch_one(const BatchArgs& g, int sms, cudaStream_t s)
     if (hb < 1) hb = 1;
     batch_heavy_kernel<D, NS, DENSE, EXACT><<<(int)hb, kThreads, 0, s>>>(g);
     count_launches(1);
+    kernel_mark(group_phase_name(D, NS, DENSE, EXACT, true), s);
     return cudaGetLastError();
 }
 

@@ -426,9 +426,12 @@ class Batch:
         pa, kp = _ptr_array(pred)
         return (m, k, md, qa, ia, da, pa), (kq, ki, kd, kp)
 
-    def query(self, queries, ks, modes, flags: int = 0, stream=None):
-        """Query every index; returns lists (ids, dist2, pred) with one entry per index."""
-        ids, d2, pred = self._outputs(queries, ks, modes)
+    def query(self, queries, ks, modes, flags: int = 0, stream=None, out=None):
+        """Query every index; returns lists (ids, dist2, pred) with one entry per index.
+
+        Queries and outputs may be host arrays or device tensors; `out`, if
+        given, is (ids, dist2, pred) lists of caller buffers to fill."""
+        ids, d2, pred = self._outputs(queries, ks, modes) if out is None else out
         (m, k, md, qa, ia, da, pa), keep = self._arrays(queries, ks, modes, ids, d2, pred)
         _check(library().knn_batch_query(self._h, qa, m, k, md, ia, da, pa, flags,
                                          _stream(stream, *queries)))
@@ -508,12 +511,12 @@ def knn_timing_enable(on: bool = True):
 
 
 def knn_timing_read() -> list[tuple[str, float]]:
-    """Phases of this thread's oldest unread build / query (of its last 64, while
-    timing is on): [(name, device ms)], or [] when none is unread."""
-    names = (ctypes.c_char_p * 16)()
-    ms = (ctypes.c_float * 16)()
-    cnt = library().knn_timing_read(names, ms, 16)
-    return [(names[i].decode(), float(ms[i])) for i in range(min(cnt, 16))]
+    """Phases of this thread's oldest unread call (of its last 32, while timing
+    is on): [(name, device ms)], or [] when none is unread."""
+    names = (ctypes.c_char_p * 40)()
+    ms = (ctypes.c_float * 40)()
+    cnt = library().knn_timing_read(names, ms, 40)
+    return [(names[i].decode(), float(ms[i])) for i in range(min(cnt, 40))]
 
 
 def knn_kernel_launches() -> int:

@@ -56,7 +56,7 @@ def test_aggregate_single():
 
 def test_defaults_meet_the_timing_rules():
     a = bench.parse_args([])
-    assert a.gpus == 1 and a.warmup >= 3 and a.steps >= 1 and a.config == "large_cls"
+    assert a.gpus == 1 and a.warmup >= 3 and a.steps >= 1 and a.config == "batched"
 
 
 def test_method_bytes_counts_each_term():
@@ -70,33 +70,58 @@ def test_method_bytes_counts_each_term():
     assert bench.method_bytes(w, stats, 4, 1) == 2 * 56 + 12 * 8 + 100 * 16
 
 
-def test_profiled_traffic_ignores_stale_summaries(tmp_path, monkeypatch):
-    p = tmp_path / "q_large_cls.md"
-    p.write_text("workload: large_cls\nkernel_source_sha256_16: 0000\n"
-                 "dram_bytes_per_launch: 123\n")
-    monkeypatch.setattr(bench, "PROFILE_SUMMARY", str(tmp_path / "q_{}.md"))
-    assert bench.profiled_traffic("large_cls") is None
-    p.write_text(f"workload: large_cls\nkernel_source_sha256_16: {bench.query_kernel_sha()}\n"
-                 "dram_bytes_per_launch: 123\n")
+def _summary(workload, phase, sha, dram=123, extra=""):
+    return (f"workload: {workload}\nphase: {phase}\nkernel_source_sha256_16: {sha}\n"
+            f"dram_bytes_per_launch: {dram}\n{extra}")
+
+
+def test_profiled_ignores_stale_summaries(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "PROFILES", str(tmp_path))
+    p = tmp_path / "q_large_cls_ncu.md"
+    p.write_text(_summary("large_cls", "query.search", "0000"))
+    assert bench.profiled("large_cls", "query.search") is None
+    p.write_text(_summary("large_cls", "query.search", bench.query_kernel_sha(),
+                          extra="issue_active_pct: 80.5\nwarp_inst_per_query: 5010\n"))
+    got = bench.profiled("large_cls", "query.search")
+    assert got["dram_bytes_per_launch"] == 123.0 and got["warp_inst_per_query"] == 5010.0
     assert bench.profiled_traffic("large_cls") == 123.0
-    assert bench.profiled_traffic("skewed_reg") is None  # no summary for it
-    # a summary filed under one workload's name but taken on another
-    (tmp_path / "q_tiny.md").write_text(
-        f"workload: large_cls\nkernel_source_sha256_16: {bench.query_kernel_sha()}\n"
-        "dram_bytes_per_launch: 123\n")
-    assert bench.profiled_traffic("tiny") is None
+    assert bench.profiled("skewed_reg", "query.search") is None  # no summary for it
+    assert bench.profiled("large_cls", "query.coop") is None     # another kernel
 
 
-def test_committed_summaries_match_their_names():
+def test_roofline_uses_measured_traffic_and_issue_rate(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "PROFILES", str(tmp_path))
+    (tmp_path / "b_ncu.md").write_text(_summary(
+        "batched", "query.d6.k32.hash", bench.query_kernel_sha(), dram=2.0e8,
+        extra="bound: issue\nissue_active_pct: 88.8\nwarp_inst_per_query: 20000\n"))
+    peaks = {"hbm_gbs": 6800.0}
+    r = bench.roofline("batched", "query.d6.k32.hash", 40.0, 1_000_000, 1.0e11, peaks,
+                       "measured", {"sm_mhz": 2000.0}, 50.0)
+    assert r["kernel"] == "qk::batch_query_kernel<6, 1, 0, 0>"
+    assert r["bound"] == "issue"
+    assert r["achieved"] == pytest.approx(2.0e8 / 0.040 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6800.0)
+    assert r["method_bytes_per_s"] == pytest.approx(1.0e11 / 0.040 / 1e9)
+    assert r["cross_check"]["below_peak"]
+    ipk = 152 * 4 * 2000.0e6
+    assert r["issue"]["frac"] == pytest.approx(20000 * 1_000_000 / 0.040 / ipk)
+    # no profile on the current source: no DRAM figure, no fraction
+    r = bench.roofline("batched", "query.d2.k32.dense", 4.0, 10, 1.0e9, peaks, "measured",
+                       None, 50.0)
+    assert r["traffic"] is None and r["frac"] is None and r["bound"] is None
+
+
+def test_kernel_names_of_phases():
+    assert bench.kernel_of_phase("query.d3.k64.dense.coop") == "qk::batch_heavy_kernel<3, 2, 1, 0>"
+    assert bench.kernel_of_phase("query.d4.k32.hash.exact") == "qk::batch_query_kernel<4, 1, 0, 1>"
+    assert bench.kernel_of_phase("build.sort").startswith("radix_hist_kernel")
+
+
+def test_committed_summaries_name_their_workload():
     import glob
-    import re
-    for path in glob.glob(os.path.join(ROOT, "profiles", "query_kernel_*_ncu.md")):
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*_ncu.md")):
         text = open(path).read()
-        wk = re.search(r"workload:\s*(\S+)", text)
-        assert wk, path
-        name = os.path.basename(path)[len("query_kernel_"):-len("_ncu.md")]
-        if name in ("large_cls", "skewed_reg", "tiny"):
-            assert wk.group(1) == name, path
+        assert bench._field(text, "workload"), path
 
 
 def test_query_order_per_workload():
@@ -129,3 +154,16 @@ def test_reference_arm_other_ranks_exit_quietly():
                         "--steps", "1", "--warmup", "0"], cwd=ROOT, env=env,
                        capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_reference_arm_batched_times_a_fixed_sample():
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--batch-count", "6",
+                        "--ref-step-seconds", "0.2", "--steps", "2", "--warmup", "1"], cwd=ROOT,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr
+    d = json.loads([l for l in r.stdout.splitlines() if l.strip()][-1])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC_BATCHED
+    assert d["config"]["workload"] == "batched" and d["config"]["sample_problems"] >= 1
+    # the line's value is the sample's queries over the time the steps took
+    q = d["config"]["sample_queries"]
+    assert d["value"] == pytest.approx(q / (d["ms_per_step"] * 1e-3), rel=1e-6)

@@ -160,3 +160,78 @@ def test_autotuner_picks_the_cheapest_candidate():
     assert c.width in [w for w, _ in c.tried]
     assert c.est_ms == min(t for _, t in c.tried)
     assert len(c.tried) >= 3
+
+
+# problems of the 256-problem batched workload: the heaviest d=6 one (problem
+# 100, n = 1,382,810, k = 15), the largest of each dimension, and k = 32 ones
+# from 1,432 to 1,864,855 points
+_FULL_SUBSET = [100, 206, 9, 20, 38, 199, 107, 12, 1, 7, 23, 57, 44]
+
+
+def test_full_size_batched_subset_matches_the_oracle():
+    """A subset of the real batched workload in one batch, with the
+    autotuner's widths, in the bench's launch configuration: a seeded sample
+    of each problem's queries equals the oracle element by element, and every
+    query equals the plain form."""
+    from paper_2004_02290_gb300 import autotune
+
+    ps = wl.gen_batched(256, seed=3)
+    sub = [ps[i] for i in _FULL_SUBSET]
+    dev = torch.device("cuda:0")
+    widths = [autotune.tune_width(p.points, p.labels, p.queries, p.k, p.mode, dev=dev).width
+              for p in sub]
+    b = knn.knn_batch_build([_dev(p.points) for p in sub], [_dev(p.labels) for p in sub],
+                            widths)
+    bids, bd2, bpred = b.query([_dev(p.queries) for p in sub], [p.k for p in sub],
+                               [p.mode for p in sub], flags=knn.KNN_QUERY_CHECKED)
+    torch.cuda.synchronize()
+    b.free()
+    rng = np.random.default_rng(2024)
+    for j, (p, w) in enumerate(zip(sub, widths)):
+        ids, d2, pred = bids[j].cpu().numpy(), bd2[j].cpu().numpy(), bpred[j].cpu().numpy()
+        pick = np.sort(rng.choice(p.m, size=min(p.m, 300), replace=False))
+        g = oracle.Grid(p.points, p.labels, w)
+        e_ids, e_d2, e_pred = g.query(p.queries[pick], p.k, p.mode)
+        g.close()
+        where = f"problem {_FULL_SUBSET[j]} (n={p.n}, d={p.d}, k={p.k}, w={w})"
+        assert np.array_equal(ids[pick], e_ids), where
+        assert np.array_equal(d2[pick].view(np.uint32), e_d2.view(np.uint32)), where
+        assert np.array_equal(pred[pick].view(np.uint32), e_pred.view(np.uint32)), where
+        idx = knn.knn_build(_dev(p.points), _dev(p.labels), w)
+        pi, pd, pp = idx.query(_dev(p.queries), p.k, p.mode, flags=knn.KNN_QUERY_CHECKED)
+        torch.cuda.synchronize()
+        idx.free()
+        assert np.array_equal(pi.cpu().numpy(), ids), where
+        assert np.array_equal(pp.cpu().numpy().view(np.uint32), pred.view(np.uint32)), where
+
+
+def test_batch_with_host_buffers_matches_device_buffers():
+    """knn_batch_build / knn_batch_query with host inputs, pinned and
+    pageable host outputs equal the all-device call."""
+    ps, _ = _problems()
+    ps = ps[:8]
+    ws = [p.w for p in ps]
+    ks = [p.k for p in ps]
+    modes = [p.mode for p in ps]
+    b = knn.knn_batch_build([_dev(p.points) for p in ps], [_dev(p.labels) for p in ps], ws)
+    ref = b.query([_dev(p.queries) for p in ps], ks, modes, flags=knn.KNN_QUERY_CHECKED)
+    torch.cuda.synchronize()
+    b.free()
+    for pinned in (True, False):
+        def host(a):
+            t = torch.from_numpy(np.ascontiguousarray(a))
+            return t.pin_memory() if pinned else t
+        b = knn.knn_batch_build([host(p.points) for p in ps], [host(p.labels) for p in ps], ws)
+        out = ([host(np.zeros((p.m, p.k), np.int32)) for p in ps],
+               [host(np.zeros((p.m, p.k), np.float32)) for p in ps],
+               [None if p.mode < 0 else host(np.zeros(p.m, np.int32 if p.mode == knn.KNN_VOTE
+                                                      else np.float32)) for p in ps])
+        b.query([host(p.queries) for p in ps], ks, modes, flags=knn.KNN_QUERY_CHECKED, out=out)
+        b.free()
+        for j in range(len(ps)):
+            assert np.array_equal(out[0][j].numpy(), ref[0][j].cpu().numpy())
+            assert np.array_equal(out[1][j].numpy().view(np.uint32),
+                                  ref[1][j].cpu().numpy().view(np.uint32))
+            if out[2][j] is not None:
+                assert np.array_equal(out[2][j].numpy().view(np.uint32),
+                                      ref[2][j].cpu().numpy().view(np.uint32))

@@ -468,6 +468,63 @@ def test_layer_cap_reports_limit():
     assert neg > 0
 
 
+def test_default_work_bound_trips_on_a_grid_far_finer_than_k_th_distance():
+    """2,000 points in the unit square on cells of 1e-5: the 8th neighbour is
+    about 0.036 away, some 3,600 layers out.  The default bound (2^22 rows
+    enumerated; in 2-D, layer L has 2L + 1 rows) ends each walk after about
+    2,048 layers: KNN_ELIMIT under KNN_QUERY_CHECKED, -1 / +inf rows, and the
+    call returns within seconds."""
+    import time
+
+    rng = np.random.default_rng(77)
+    x = rng.random((2000, 2)).astype(np.float32)
+    lab = rng.integers(0, 3, 2000).astype(np.int32)
+    q = rng.random((16, 2)).astype(np.float32)
+    idx = knn.knn_build(_dev(x), _dev(lab), 1e-5)
+    t0 = time.perf_counter()
+    with pytest.raises(knn.KnnError) as e:
+        idx.query(_dev(q), 8, knn.KNN_VOTE, flags=knn.KNN_QUERY_CHECKED)
+    assert e.value.code == knn.KNN_ELIMIT
+    assert time.perf_counter() - t0 < 30.0
+    ids, d2, _ = idx.query(_dev(q), 8, knn.KNN_VOTE)
+    torch.cuda.synchronize()
+    assert (ids.cpu().numpy() == -1).all() and np.isinf(d2.cpu().numpy()).all()
+    idx.free()
+
+
+def test_work_bound_override():
+    """GHN_MAX_ROWS replaces the default bound: 3 rows stop every walk that
+    needs layer 1 (3 rows in 2-D after the central row)."""
+    code = (
+        "import numpy as np, torch\n"
+        "from paper_2004_02290_gb300 import knn, workloads as wl\n"
+        "x, lab, q = wl.uniform(5000, 200, 2, seed=2)\n"
+        "idx = knn.knn_build(torch.from_numpy(x).cuda(), torch.from_numpy(lab).cuda(), 0.01)\n"
+        "try:\n"
+        "    idx.query(torch.from_numpy(q).cuda(), 8, flags=knn.KNN_QUERY_CHECKED)\n"
+        "    print('NOFAIL')\n"
+        "except knn.KnnError as e:\n"
+        "    print('CODE', e.code)\n")
+    r = _child(code, {"GHN_MAX_ROWS": "3"})
+    assert r.returncode == 0, r.stderr
+    assert "CODE 4" in r.stdout, r.stdout
+    r = _child(code, {"GHN_MAX_ROWS": "0"})  # no bound
+    assert r.returncode == 0, r.stderr
+    assert "NOFAIL" in r.stdout, r.stdout
+
+
+@pytest.mark.skipif(not torch.cuda.is_available() or torch.cuda.device_count() < 2,
+                    reason="needs a second GPU")
+def test_buffers_of_another_gpu_are_refused():
+    x, lab, q = wl.uniform(1000, 8, 2, seed=3)
+    idx = knn.knn_build(_dev(x), _dev(lab), 0.05)
+    q1 = torch.from_numpy(q).to("cuda:1")
+    with pytest.raises(knn.KnnError) as e:
+        idx.query(q1, 3, knn.KNN_VOTE, flags=knn.KNN_QUERY_CHECKED)
+    assert e.value.code == knn.KNN_EINVAL
+    idx.free()
+
+
 # ---- full-size workloads, in the benchmark's launch configuration, sampled ----
 
 def _sampled_full(name, sample, flags):

@@ -7,7 +7,9 @@ on two calls in a row that share the library's fixed scratch array.  This file
 is collected last, so a failure here stops a -x run only after every other
 test has run.
 """
-import ctypes
+import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -20,6 +22,7 @@ from paper_2004_02290_gb300 import workloads as wl
 pytestmark = pytest.mark.gpu
 
 MEAN_RTOL = 1e-6
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -101,3 +104,41 @@ def test_noalloc_rejects_too_many_queries_and_host_buffers():
     assert rc == knn.KNN_EINVAL
     assert b"device memory" in lib.knn_last_error()
     idx.free()
+
+
+_ALL_DEFERRED = r"""
+import numpy as np, torch
+from paper_2004_02290_gb300 import knn, workloads as wl
+def dev(a): return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+lib = knn.library()
+w = wl.make("skewed_reg", n=50_000, m=3000, w=0.03)
+idx = knn.knn_build(dev(w.points), dev(w.labels), w.w)
+bad = 0
+for q in (dev(w.queries), dev(w.queries[::-1][:1200])):
+    ids, d2, pred = idx.query(q, w.k, w.mode, flags=knn.KNN_QUERY_CHECKED)
+    m = q.shape[0]
+    ids2 = torch.full((m, w.k), -7, dtype=torch.int32, device="cuda")
+    d22 = torch.full((m, w.k), -7.0, dtype=torch.float32, device="cuda")
+    pred2 = torch.full((m,), -7.0, dtype=torch.float32, device="cuda")
+    rc = lib.knn_query_noalloc(idx.handle, q.data_ptr(), m, w.k, w.mode, ids2.data_ptr(),
+                               d22.data_ptr(), pred2.data_ptr(), knn.KNN_QUERY_CHECKED,
+                               torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    bad += rc != 0
+    bad += not torch.equal(ids, ids2)
+    bad += not torch.equal(d2.view(torch.int32), d22.view(torch.int32))
+    bad += not torch.equal(pred.view(torch.int32), pred2.view(torch.int32))
+idx.free()
+print("BAD", bad)
+"""
+
+
+def test_noalloc_every_query_deferred():
+    """Every query handed to the cooperative kernel, whose list of deferred
+    queries is in the fixed array: both calls, the second shorter, must still
+    equal knn_query bit for bit."""
+    env = dict(os.environ, GHN_HEAVY_ROWS="2", GHN_HEAVY_CANDS="8")
+    r = subprocess.run([sys.executable, "-c", _ALL_DEFERRED], cwd=ROOT, env=env,
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-3000:]
+    assert "BAD 0" in r.stdout, r.stdout
