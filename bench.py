@@ -658,8 +658,8 @@ def run_ours(args):
 
 
 def build_phase_bytes(phase, w, info):
-    """Algorithmic bytes of a build phase over n points (SURVEY-style per-point
-    figures): box and keys read the points, the sort reads and writes
+    """Algorithmic bytes of a build phase over n points, from per-point
+    figures: box and keys read the points, the sort reads and writes
     (key, index) pairs per pass, the gather reads a point and writes its row,
     row id and label."""
     n, d = w.n, w.d

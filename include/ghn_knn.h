@@ -121,7 +121,7 @@ knn_status knn_build(const float* points, const void* labels, int64_t n, int32_t
 
 /*
  * knn_build_grid: knn_build with one cell measurement per dimension (Sec.
- * III.A: cells are identical but not necessarily equilateral).
+ * III.A: all cells have one shape, which need not be a cube).
  *   cell_widths  host, d positive finite widths.
  *   splits       host, d split counts in [1, 2^31), or NULL: training cells
  *                are clamped to splits[j] - 1, so that the largest value lies
@@ -213,7 +213,11 @@ knn_status knn_query_stats(const ghn_index* index, const float* queries, int64_t
  * The kernels' scratch lives in a fixed device array of the library (about
  * 4 MiB, held by every GPU that loads the library until exit).  The first call
  * on a device looks up that array's address, with the index's device current;
- * make that first call before any stream capture.  All calls share the array:
+ * make that first call before any stream capture.  The address is kept for the
+ * life of the process: a cudaDeviceReset in between invalidates it (and every
+ * index on that device), so do not use the library across a device reset.
+ * Queries, ids, dist2 and pred must be device memory of the index's GPU
+ * (KNN_EINVAL otherwise).  All calls share the array:
  * calls whose work overlaps on the GPU race on it and must be ordered (one
  * stream, or synchronised).  No memory is allocated or freed by this call.
  */

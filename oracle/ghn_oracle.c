@@ -24,8 +24,8 @@
  * the design notes of the repository):
  *   origin    per-dimension minimum of the training points (splits cover the
  *             range of values, Sec. III.A).
- *   widths    one cell measurement w_j per dimension (Sec. III.A: cells are
- *             identical but not necessarily equilateral); a scalar width is
+ *   widths    one cell measurement w_j per dimension (Sec. III.A: all cells
+ *             have one shape, which need not be a cube); a scalar width is
  *             the case w_j = w for every j.
  *   splits    when a grid comes from the paper's cell measurement (s_j equal
  *             splits of each range, the last one closed), training cells are

@@ -17,8 +17,8 @@
 // Candidates.  The warp flattens the ranges of 32 rows and streams their
 // points with coalesced 8/16/32-byte loads, several chunks of 32 in flight.
 //
-// k-buffer ("a heap of size k", Sec. III.B).  Sorted 64-bit keys (squared
-// distance bits << 32 | training index) over the lanes, one key per lane for
+// k-buffer (the paper keeps the k best in a heap, Sec. III.B).  Sorted 64-bit
+// keys (squared distance bits << 32 | training index) over the lanes, one key per lane for
 // k <= 32 and two for k <= 64.  Squared distances are non-negative floats, so
 // unsigned order of the keys is the order (distance, index).  Few entering
 // candidates are inserted one by one (ballot and shift); many are sorted
@@ -448,6 +448,17 @@ __device__ __forceinline__ unsigned long long layer_rows(const Layer<D>& b)
     return nrows;
 }
 
+// x / e for x < 2^16 and 1 <= e < 2^31, from a single-precision reciprocal
+// of e: the estimate is within 1/64 of x / e, so one step each way corrects
+// it (no integer division on the walk's path).
+__device__ __forceinline__ unsigned int udiv_small(unsigned int x, unsigned int e, float inv_e)
+{
+    unsigned int q = (unsigned int)((float)x * inv_e);
+    if (q * e > x) --q;
+    if ((q + 1u) * e <= x) ++q;
+    return q;
+}
+
 // Row odometer over the outer axes 0..D-2 of the layer box, last outer axis
 // fastest: digits of the starting row and of the stride between visits.
 template <int D>
@@ -455,15 +466,19 @@ struct RowWalk {
     int dig[D > 1 ? D - 1 : 1];
     int inc[D > 1 ? D - 1 : 1];
 
+    // first and step are below 2^16 (a lane or thread and the warp or block size)
     __device__ __forceinline__ void start(const Layer<D>& b, unsigned int first, unsigned int step)
     {
 #pragma unroll
         for (int j = D - 2; j >= 0; --j) {
             const unsigned int e = (unsigned int)(b.hi[j] - b.lo[j] + 1);
-            dig[j] = (int)(first % e);
-            first /= e;
-            inc[j] = (int)(step % e);
-            step /= e;
+            const float inv = __frcp_rn((float)e);
+            const unsigned int qf = udiv_small(first, e, inv);
+            const unsigned int qs = udiv_small(step, e, inv);
+            dig[j] = (int)(first - qf * e);
+            first = qf;
+            inc[j] = (int)(step - qs * e);
+            step = qs;
         }
     }
     __device__ __forceinline__ void advance(const Layer<D>& b)
@@ -553,27 +568,6 @@ __device__ __forceinline__ void row_ranges(const QueryArgs& a, unsigned long lon
         la = lb;
         lb = 0u;
     }
-}
-
-// Key (squared distance bits << 32 | training index) of the stored row `pos`,
-// or kEmptyKey when it cannot beat the k-th key (open: the buffer is not full).
-template <int D>
-__device__ __forceinline__ unsigned long long candidate_key(const QueryArgs& a, const Query<D>& s,
-                                                            unsigned int pos, bool open,
-                                                            float kth_d)
-{
-    constexpr int P = row_floats(D);
-    Row<P> row;
-    row.load(a.rows, pos);
-    const unsigned int rid = __ldg(a.rid + pos);
-    float acc = 0.0f;
-#pragma unroll
-    for (int j = 0; j < D; ++j) {
-        const float dj = __fsub_rn(s.q[j], row.v[j]);
-        acc = __fadd_rn(acc, __fmul_rn(dj, dj));
-    }
-    if (!(open || acc <= kth_d)) return kEmptyKey;
-    return ((unsigned long long)__float_as_uint(acc) << 32) | rid;
 }
 
 // Offer one key per lane to the buffer; true when some key entered it.  Keys
@@ -740,9 +734,12 @@ __device__ __forceinline__ void write_outputs(const QueryArgs& a, long long qid,
 // the register cap spills a little to L1 (measured: 8 blocks on the d=3 and
 // d=4 workloads; 6 for d=5 and 6, 3% faster than 4 on the heaviest d=6
 // problems; 4 for the larger query state of d=7 and 8).
+#ifndef GHN_MIN_BLOCKS_D4
+#define GHN_MIN_BLOCKS_D4 8
+#endif
 template <int D, int NS>
 struct MinBlocks {
-    static constexpr int value = NS == 1 ? (D <= 4 ? 8 : (D <= 6 ? 6 : 4)) : 2;
+    static constexpr int value = NS == 1 ? (D <= 4 ? GHN_MIN_BLOCKS_D4 : (D <= 6 ? 6 : 4)) : 2;
 };
 
 // Per-warp shared memory of the walk: the lanes' ranges of one row batch.
@@ -768,15 +765,6 @@ __device__ __forceinline__ unsigned int owner_of(const unsigned int* end, unsign
             lo_l = mid + 1;
     }
     return (unsigned int)lo_l;
-}
-
-// Row position of flattened candidate t, held by lane `own`'s ranges.
-__device__ __forceinline__ unsigned int pos_in(const WarpSmem& sm, unsigned int own,
-                                               unsigned int t)
-{
-    const unsigned int off = t - sm.beg[own];
-    const unsigned int ln = sm.la[own];
-    return off < ln ? sm.a[own] + off : sm.b[own] + (off - ln);
 }
 
 // One query by one warp.  Returns true when the query was deferred to the
@@ -851,41 +839,69 @@ __device__ __forceinline__ bool walk_query(const QueryArgs& a, long long qid, Wa
                 // chunks of 32 candidates; the next chunk's rows are loaded
                 // while the current one is offered to the buffer
                 constexpr int P = row_floats(D);
+                // each lane's cursor: the lane `own` whose ranges hold its
+                // next candidate (a binary search for the first chunk, then
+                // forward moves only when a chunk step leaves own's ranges)
+                // and a copy of own's ranges
+                unsigned int own = 0u, o_end = 0u, o_beg = 0u, o_la = 0u, o_a = 0u, o_b = 0u;
                 Row<P> nrow;
-                unsigned int nrid = 0u;
-                // own: the lane whose ranges hold this lane's next candidate,
-                // found by binary search for the first chunk and then moved
-                // forward (positions only grow, by 32 a chunk)
-                unsigned int own = 0u;
+                unsigned int npos = 0u;
                 if (lane < total) {
                     own = owner_of(sm.end, lane);
-                    const unsigned int pos = pos_in(sm, own, lane);
-                    nrow.load(a.rows, pos);
-                    nrid = __ldg(a.rid + pos);
+                    o_end = sm.end[own];
+                    o_beg = sm.beg[own];
+                    o_la = sm.la[own];
+                    o_a = sm.a[own];
+                    o_b = sm.b[own];
+                    const unsigned int off = (unsigned int)lane - o_beg;
+                    npos = off < o_la ? o_a + off : o_b + (off - o_la);
+                    nrow.load(a.rows, npos);
                 }
+                // the k-th squared distance (+inf while the buffer is short)
+                float kf = tk.count == tk.k ? __uint_as_float((unsigned)(tk.kth >> 32)) : INFINITY;
                 for (unsigned int cb = 0; cb < total; cb += 32u) {
                     const unsigned int t = cb + lane;
                     const Row<P> row = nrow;
-                    const unsigned int rid = nrid;
-                    if (t + 32u < total) {
-                        const unsigned int tn = t + 32u;
-                        while (sm.end[own] <= tn) ++own;  // ends at 31 at the latest
-                        const unsigned int pos = pos_in(sm, own, tn);
-                        nrow.load(a.rows, pos);
-                        nrid = __ldg(a.rid + pos);
+                    const unsigned int pos = npos;
+                    const unsigned int tn = t + 32u;
+                    if (tn < total) {
+                        if (tn >= o_end) {
+                            do {
+                                ++own;
+                            } while (sm.end[own] <= tn);  // ends at 31 at the latest
+                            o_end = sm.end[own];
+                            o_beg = sm.beg[own];
+                            o_la = sm.la[own];
+                            o_a = sm.a[own];
+                            o_b = sm.b[own];
+                        }
+                        const unsigned int off = tn - o_beg;
+                        npos = off < o_la ? o_a + off : o_b + (off - o_la);
+                        nrow.load(a.rows, npos);
                     }
-                    unsigned long long key = kEmptyKey;
+                    bool pass = false;
+                    float acc = 0.0f;
                     if (t < total) {
-                        float acc = 0.0f;
 #pragma unroll
                         for (int j = 0; j < D; ++j) {
                             const float dj = __fsub_rn(s.q[j], row.v[j]);
                             acc = __fadd_rn(acc, __fmul_rn(dj, dj));
                         }
-                        if (tk.kth == kEmptyKey || acc <= __uint_as_float((unsigned)(tk.kth >> 32)))
-                            key = ((unsigned long long)__float_as_uint(acc) << 32) | rid;
+                        pass = acc <= kf;
                     }
-                    updated |= offer(tk, key, lane);
+                    // the training index is read only for the candidates that
+                    // pass the distance test; the key's order then decides
+                    if (__ballot_sync(FULL, pass)) {
+                        const unsigned long long key =
+                            pass ? ((unsigned long long)__float_as_uint(acc) << 32) |
+                                       __ldg(a.rid + pos)
+                                 : kEmptyKey;
+                        if (offer(tk, key, lane)) {
+                            updated = true;
+                            kf = tk.count == tk.k ? __uint_as_float((unsigned)(tk.kth >> 32))
+                                                  : INFINITY;
+                        }
+                    }
                 }
                 __syncwarp();
             }
@@ -1069,26 +1085,46 @@ __device__ __forceinline__ void coop_query(const QueryArgs& a, long long qid, Co
                 unsigned int total = 0u;
                 for (int w2 = 0; w2 < kWarps; ++w2) total += sm.wsum[w2];
                 __syncthreads();
-                // the candidates, 32 per warp at a time
+                // the candidates, 32 per warp at a time; each thread keeps the
+                // range of its last candidate and searches forward from it
+                unsigned int r_own = 0u;
                 for (unsigned int cb = 32u * wib; cb < total; cb += 32u * kWarps) {
                     const unsigned int t = cb + lane;
-                    unsigned long long key = kEmptyKey;
+                    bool pass = false;
+                    float acc = 0.0f;
+                    unsigned int pos = 0u;
                     if (t < total) {
-                        unsigned int lo_r = 0u, hi_r = nr - 1u;  // first range ending past t
-                        while (lo_r < hi_r) {
-                            const unsigned int mid = (lo_r + hi_r) >> 1;
-                            if (sm.r_end[mid] > t)
-                                hi_r = mid;
-                            else
-                                lo_r = mid + 1u;
+                        if (sm.r_end[r_own] <= t) {
+                            // first range ending past t, after r_own
+                            unsigned int lo_r = r_own + 1u, hi_r = nr - 1u;
+                            while (lo_r < hi_r) {
+                                const unsigned int mid = (lo_r + hi_r) >> 1;
+                                if (sm.r_end[mid] > t)
+                                    hi_r = mid;
+                                else
+                                    lo_r = mid + 1u;
+                            }
+                            r_own = lo_r;
                         }
-                        const unsigned int pos =
-                            sm.r_start[lo_r] + (t - (sm.r_end[lo_r] - sm.r_len[lo_r]));
+                        pos = sm.r_start[r_own] + (t - (sm.r_end[r_own] - sm.r_len[r_own]));
+                        constexpr int P = row_floats(D);
+                        Row<P> row;
+                        row.load(a.rows, pos);
+#pragma unroll
+                        for (int j = 0; j < D; ++j) {
+                            const float dj = __fsub_rn(s.q[j], row.v[j]);
+                            acc = __fadd_rn(acc, __fmul_rn(dj, dj));
+                        }
                         const unsigned long long ek2 = tk.kth < gkth ? tk.kth : gkth;
-                        key = candidate_key<D>(a, s, pos, ek2 == kEmptyKey,
-                                               __uint_as_float((unsigned)(ek2 >> 32)));
+                        pass = ek2 == kEmptyKey || acc <= __uint_as_float((unsigned)(ek2 >> 32));
                     }
-                    offer(tk, key, lane, gkth);
+                    if (__ballot_sync(FULL, pass)) {
+                        const unsigned long long key =
+                            pass ? ((unsigned long long)__float_as_uint(acc) << 32) |
+                                       __ldg(a.rid + pos)
+                                 : kEmptyKey;
+                        offer(tk, key, lane, gkth);
+                    }
                 }
                 __syncthreads();
             }
@@ -1243,11 +1279,11 @@ __global__ void __launch_bounds__(kThreads, 1) batch_heavy_kernel(const BatchArg
 }
 
 template <class Kernel>
-int blocks_per_sm(Kernel k, int& cache)
+int blocks_per_sm(Kernel k, int& cache, int threads = kThreads)
 {
     if (cache == 0) {
         int v = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k, kThreads, 0) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k, threads, 0) != cudaSuccess ||
             v < 1)
             v = 1;
         cache = v;

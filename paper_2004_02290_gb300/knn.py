@@ -74,12 +74,13 @@ class knn_server_stats_t(ctypes.Structure):
 
 
 def library(path: str | None = None) -> ctypes.CDLL:
-    """Load the CUDA library (raises if it has not been built)."""
+    """Load the CUDA library (raises if it has not been built).  GHN_LIB may
+    name another build of it (for comparing builds)."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
-        p = path or LIB_PATH
+        p = path or os.environ.get("GHN_LIB") or LIB_PATH
         if not os.path.exists(p):
             raise RuntimeError(f"CUDA library not built: {p} is missing "
                                "(run __graft_entry__.build() or build_ext.build())")

@@ -346,16 +346,18 @@ def test_phase_timing_reads_calls_oldest_first():
         q2 = knn.knn_timing_read()
         assert [n for n, _ in build] == ["stage", "box", "keys", "sort", "cells", "table",
                                          "gather"]
-        assert [n for n, _ in q1] == [n for n, _ in q2] == ["stage", "order", "search", "copy"]
+        # search: the warp or slot kernel; coop: the cooperative kernel
+        assert [n for n, _ in q1] == [n for n, _ in q2] == ["stage", "order", "search", "coop",
+                                                            "copy"]
         assert all(t >= 0.0 for _, t in build + q1 + q2)
         assert knn.knn_timing_read() == []
-        # the thread keeps its last 64 calls: the oldest unread ones are dropped
-        for _ in range(70):
+        # the thread keeps its last 32 calls: the oldest unread ones are dropped
+        for _ in range(40):
             idx.query(_dev(w.queries[:10]), 1)
         got = 0
         while knn.knn_timing_read():
             got += 1
-        assert got == 64
+        assert got == 32
         idx.free()
     finally:
         knn.knn_timing_enable(False)
@@ -469,18 +471,19 @@ def test_layer_cap_reports_limit():
 
 
 def test_default_work_bound_trips_on_a_grid_far_finer_than_k_th_distance():
-    """2,000 points in the unit square on cells of 1e-5: the 8th neighbour is
-    about 0.036 away, some 3,600 layers out.  The default bound (2^22 rows
+    """2,000 points in the unit square on cells of 2e-6: the 8th neighbour is
+    about 0.036 away, some 18,000 layers out.  The default bound (2^22 rows
     enumerated; in 2-D, layer L has 2L + 1 rows) ends each walk after about
-    2,048 layers: KNN_ELIMIT under KNN_QUERY_CHECKED, -1 / +inf rows, and the
-    call returns within seconds."""
+    2,048 layers (0.004 away, where a query expects 0.1 points): KNN_ELIMIT
+    under KNN_QUERY_CHECKED, -1 / +inf rows, and the call returns within
+    seconds."""
     import time
 
     rng = np.random.default_rng(77)
     x = rng.random((2000, 2)).astype(np.float32)
     lab = rng.integers(0, 3, 2000).astype(np.int32)
     q = rng.random((16, 2)).astype(np.float32)
-    idx = knn.knn_build(_dev(x), _dev(lab), 1e-5)
+    idx = knn.knn_build(_dev(x), _dev(lab), 2e-6)
     t0 = time.perf_counter()
     with pytest.raises(knn.KnnError) as e:
         idx.query(_dev(q), 8, knn.KNN_VOTE, flags=knn.KNN_QUERY_CHECKED)
