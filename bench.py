@@ -470,6 +470,7 @@ def kernel_of_phase(phase: str) -> str:
         "build.cells": "cells_count_kernel + cells_write_kernel",
         "build.table": "dense-table scan / hash insert kernels",
         "build.gather": "gather_kernel",
+        "build.small": "small_build_kernel (ids, sort, rows, dense table in one block)",
     }.get(phase, phase)
 
 
@@ -673,6 +674,8 @@ def build_phase_bytes(phase, w, info):
         "build.sort": passes * n * (key + 2 * (key + 4)),
         "build.cells": 2 * key * n,
         "build.gather": n * (4 + 4 * d + 4 * info.row_floats + 4 + 8),
+        # one block: read the points twice (ids, gather), write rows, row ids, table
+        "build.small": n * (8 * d + 4 * info.row_floats + 4) + 4 * (int(info.table_slots) or 0),
     }
     return float(table.get(phase, 0))
 
@@ -761,13 +764,15 @@ def batched_widths(ps, args, dev):
             saved = json.load(f)
         if len(saved["widths"]) != len(ps):
             raise SystemExit("--widths-in holds widths for another problem count")
-        return [float(x) for x in saved["widths"]], 0.0, None
+        defer = [tuple(x) for x in saved.get("deferral", [[0, 0]] * len(ps))]
+        return [float(x) for x in saved["widths"]], 0.0, None, defer
     widths, tune_s, choices = autotune.tune_batch(ps, dev=dev)
+    defer = [tuple(c.deferral) for c in choices]
     if args.widths_out:
         os.makedirs(os.path.dirname(os.path.abspath(args.widths_out)), exist_ok=True)
         with open(args.widths_out, "w") as f:
-            json.dump({"widths": widths}, f)
-    return widths, tune_s, choices
+            json.dump({"widths": widths, "deferral": [list(x) for x in defer]}, f)
+    return widths, tune_s, choices, defer
 
 
 def run_batched(args):
@@ -791,7 +796,7 @@ def run_batched(args):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     ps = wl.gen_batched(args.batch_count, seed=3)
-    widths, tune_s, choices = batched_widths(ps, args, dev)
+    widths, tune_s, choices, defer = batched_widths(ps, args, dev)
     for p_, w_ in zip(ps, widths):
         p_.w = w_
     pts = [torch.from_numpy(p_.points).to(dev) for p_ in ps]
@@ -810,15 +815,21 @@ def run_batched(args):
 
     plain_out, batch_out = outs(), outs()
 
+    tuned = [i for i, x in enumerate(defer) if tuple(x) != (0, 0)]
+
     def plain_step():
         for i, p_ in enumerate(ps):
             idx = knn.knn_build(pts[i], lab[i], p_.w)
+            if defer[i] != (0, 0):
+                idx.set_deferral(*defer[i])
             knn.knn_query(idx, qs[i], p_.k, p_.mode, ids=plain_out[0][i],
                           dist2=plain_out[1][i], pred=plain_out[2][i])
             idx.free()
 
     def batched_step():
         b = knn.knn_batch_build(pts, lab, widths)
+        for i in tuned:
+            b.set_deferral(i, *defer[i])
         b.query(qs, ks, modes, out=batch_out)
         b.free()
 
@@ -875,6 +886,8 @@ def run_batched(args):
                     for i in range(len(ps)))
     # the query alone: direct launches and a replayed CUDA graph on a built batch
     batch = knn.knn_batch_build(pts, lab, widths)
+    for i in tuned:
+        batch.set_deferral(i, *defer[i])
     q_ms = timed(lambda: batch.query(qs, ks, modes), args.steps)
     plan, gi, gd, gp = batch.plan(qs, ks, modes)
     g_ms = timed(lambda: plan.run(), args.steps)
@@ -905,7 +918,7 @@ def run_batched(args):
                     clocks, float(np.mean(b_ms)))
 
     # ---- e2e: the same batched step on pinned host buffers through the C ABI ----
-    e2e = None if args.no_e2e else run_e2e_batched(ps, widths, knn, dev, args)
+    e2e = None if args.no_e2e else run_e2e_batched(ps, widths, defer, knn, dev, args)
 
     # ---- the oracle on the host cores, on whole problems; its outputs checked ----
     cpu, oracle_check = None, None
@@ -949,22 +962,33 @@ def run_batched(args):
         "gpu_launches": int(lb), "gpu_launches_per_step": lb / args.steps,
         "query_kernel_groups": len([g for g in groups if not g.endswith(".coop")]),
         "phase_ms": {k: round(v, 4) for k, v in sorted(phase_ms.items())},
-        "autotune": autotune_summary(choices),
+        "autotune": autotune_summary(choices, defer),
         "step_ms_median": float(np.median(b_ms)),
     }), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
-def autotune_summary(choices):
-    if not choices:
-        return None
-    tried = [len(c.tried) for c in choices]
-    return {"axes": "cell width (half powers of two from an occupancy guess)",
-            "candidates_per_problem_mean": float(np.mean(tried))}
+def autotune_summary(choices, defer):
+    """What the tuner chose: widths tried per problem and the threads-per-query
+    setting (deferral to the 256-thread cooperative kernel) per problem."""
+    from paper_2004_02290_gb300 import autotune
+
+    names = {(0, 0): "default deferral", (0, -1): "no deferral by candidates",
+             (-1, -1): "one warp for every query"}
+    counts = {}
+    for x in defer:
+        key = names.get(tuple(x), str(tuple(x)))
+        counts[key] = counts.get(key, 0) + 1
+    out = {"axes": ["cell width (half powers of two from an occupancy guess)",
+                    "threads per heavy query: deferral settings " + str(autotune.DEFERRALS)],
+           "deferral_choices": counts}
+    if choices:
+        out["widths_tried_per_problem_mean"] = float(np.mean([len(c.tried) for c in choices]))
+    return out
 
 
-def run_e2e_batched(ps, widths, knn, dev, args):
+def run_e2e_batched(ps, widths, defer, knn, dev, args):
     """The batched step through the C ABI with pinned host buffers: every
     step copies all problems' points, labels and queries in, and writes every
     output to host memory (the query returns once they are filled)."""
@@ -984,6 +1008,9 @@ def run_e2e_batched(ps, widths, knn, dev, args):
 
     def step():
         b = knn.knn_batch_build(pts, lab, widths)
+        for i, x in enumerate(defer):
+            if tuple(x) != (0, 0):
+                b.set_deferral(i, *x)
         b.query(qs, ks, modes, out=out)
         b.free()
         torch.cuda.synchronize(dev)
@@ -1021,12 +1048,15 @@ def run_profile_case(args):
     knn.knn_timing_enable(True)
     if args.config == "batched" and args.batched_problem is None:
         ps = wl.gen_batched(args.batch_count, seed=3)
-        widths, _, _ = batched_widths(ps, args, dev)
+        widths, _, _, defer = batched_widths(ps, args, dev)
         pts = [torch.from_numpy(p_.points).to(dev) for p_ in ps]
         lab = [torch.from_numpy(p_.labels).to(dev) for p_ in ps]
         qs = [torch.from_numpy(p_.queries).to(dev) for p_ in ps]
         for _ in range(args.repeat):
             b = knn.knn_batch_build(pts, lab, widths)
+            for i, x in enumerate(defer):
+                if tuple(x) != (0, 0):
+                    b.set_deferral(i, *x)
             b.query(qs, [p_.k for p_ in ps], [p_.mode for p_ in ps],
                     flags=knn.KNN_QUERY_CHECKED)
             b.free()

@@ -319,6 +319,22 @@ int32_t knn_timing_read(const char** names, float* ms, int32_t cap);
 /* Kernels this library has launched in this process (all threads). */
 int64_t knn_kernel_launches(void);
 
+/*
+ * Deferral of heavy queries (a tuning choice; results do not depend on it).
+ * The warp kernel walks a query with one warp; a query whose layer has more
+ * than `heavy_rows` cell rows, or whose batch of 32 rows holds more than
+ * `heavy_cands` points, is handed to the cooperative kernel, which walks it
+ * with a block of 256 threads.  0 keeps the library default (1024 rows for
+ * d <= 4, 4096 above; 8192 points; the environment variables GHN_HEAVY_ROWS
+ * and GHN_HEAVY_CANDS replace these defaults), a negative value never defers
+ * on that test, a positive value is the threshold.  knn_index_set_deferral
+ * sets it for later queries of an index, knn_batch_set_deferral for index i
+ * of a batch (later knn_batch_query and knn_batch_plan calls).
+ */
+knn_status knn_index_set_deferral(ghn_index* index, int64_t heavy_rows, int64_t heavy_cands);
+knn_status knn_batch_set_deferral(ghn_batch* batch, int32_t i, int64_t heavy_rows,
+                                  int64_t heavy_cands);
+
 /* Release the index (NULL is a no-op).  Waits for work that uses it. */
 void knn_free(ghn_index* index);
 

@@ -1,16 +1,24 @@
-"""Autotuner for the cell width of each index of a problem set.
+"""Autotuner for each index of a problem set: cell width and threads per query.
 
 The paper measures cells from the data (Sec. III.A); the library takes the
-width from the caller.  For a problem set, the tuner picks each index's width
-by measurement on the GPU: starting from a guess, it walks a grid of widths
-(half powers of two) downhill, building the index and timing a sample of the
-queries at each, and keeps the width of the least estimated time (build +
-sampled query time scaled to all queries).
-The kernels' tile shape (one warp per query, 32-candidate chunks, the
-number of resident blocks) is fixed by the design and its occupancy sweep.
+width from the caller.  For a problem set, the tuner picks each index's
+settings by measurement on the GPU:
+  - cell width: starting from a guess, it walks a grid of widths (half powers
+    of two) downhill, building the index and timing a sample of the queries
+    at each, and keeps the width of the least estimated time (build + sampled
+    query time scaled to all queries);
+  - threads per query for heavy queries: at that width, it times the sample
+    with the library's default deferral to the cooperative kernel (a block
+    of 256 threads for a query whose layers or row batches are large), with
+    no deferral by candidate count, and with no deferral at all (every query
+    on one warp of 32 threads), and keeps the fastest
+    (knn_index_set_deferral / knn_batch_set_deferral).
+The warp kernel's own tile (32 rows a batch, 32 candidates a chunk, the
+resident blocks per SM) is fixed by the design and its occupancy sweep.
 
 Every candidate runs through the same library calls as a normal query, so
 the chosen width is an input like any other: the oracle takes it unchanged.
+The deferral changes which kernel walks a query, never its result.
 """
 from __future__ import annotations
 
@@ -22,11 +30,18 @@ import numpy as np
 from . import knn
 
 
+# Deferral settings the tuner tries (heavy_rows, heavy_cands): the library's
+# default, no deferral by candidate count, no deferral.
+DEFERRALS = [(0, 0), (0, -1), (-1, -1)]
+
+
 @dataclasses.dataclass
 class Choice:
     width: float
     est_ms: float
     tried: list  # (width, est_ms)
+    deferral: tuple = (0, 0)  # (heavy_rows, heavy_cands) of knn_index_set_deferral
+    deferral_ms: list = dataclasses.field(default_factory=list)  # sample ms per DEFERRALS entry
 
 
 def start_width(points, k: int) -> float:
@@ -123,11 +138,38 @@ def tune_width(points, labels, queries, k: int, mode: int, step: float = 0.5,
     if not tried:
         raise RuntimeError("no candidate width could be built")
     best = min(tried, key=lambda t: t[1])
-    return Choice(width=best[0], est_ms=best[1], tried=tried)
+    deferral, dms = _tune_deferral(pts, lab, q, k, mode, best[0], stream)
+    return Choice(width=best[0], est_ms=best[1], tried=tried, deferral=deferral,
+                  deferral_ms=dms)
+
+
+def _tune_deferral(pts, lab, q, k, mode, w, stream, reps: int = 3):
+    """The fastest deferral setting on the sample (least of `reps` timings each)."""
+    import torch
+
+    idx = knn.knn_build(pts, lab, w)
+    md = mode if lab is not None else knn.KNN_NONE
+    times = []
+    for rows, cands in DEFERRALS:
+        idx.set_deferral(rows, cands)
+        best = None
+        for _ in range(reps):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(stream)
+            idx.query(q, k, md)
+            ev[1].record(stream)
+            ev[1].synchronize()
+            t = ev[0].elapsed_time(ev[1])
+            best = t if best is None else min(best, t)
+        times.append(best)
+    idx.free()
+    i = min(range(len(DEFERRALS)), key=lambda j: times[j])
+    return DEFERRALS[i], times
 
 
 def tune_batch(problems, dev=None):
-    """Widths for every problem; returns (widths, seconds spent, choices)."""
+    """Settings for every problem; returns (widths, seconds spent, choices)
+    (each choice also carries the problem's deferral setting)."""
     t0 = time.perf_counter()
     choices = [tune_width(p.points, p.labels, p.queries, p.k, p.mode, dev=dev) for p in problems]
     return [c.width for c in choices], time.perf_counter() - t0, choices

@@ -50,6 +50,15 @@ struct BuildDesc {
     GridConst g;
 };
 
+// The part of a descriptor the row gather reads for every row (32 bytes).
+struct __align__(16) GatherDesc {
+    const float* points;
+    long long off;
+    long long rows_off;
+    int d;
+    int p;
+};
+
 struct Tile {
     int index;
     int count;
@@ -287,21 +296,28 @@ __global__ void batch_hash_insert_kernel(const BuildDesc* __restrict__ descs, in
 // Rows into cell order, padded per index; the training index of each row
 // local to its index; the labels of every index.
 __global__ void __launch_bounds__(256)
-    batch_gather_kernel(const BuildDesc* __restrict__ descs, int shift, long long total,
+    batch_gather_kernel(const GatherDesc* __restrict__ descs, int shift, long long total,
                         const unsigned long long* __restrict__ keys,
                         const unsigned int* __restrict__ vals, float* __restrict__ rows,
                         unsigned int* __restrict__ rid)
 {
     for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < total;
          r += (long long)gridDim.x * blockDim.x) {
-        const BuildDesc& ds = descs[keys[r] >> shift];
+        const GatherDesc ds = descs[keys[r] >> shift];
         const long long local = r - ds.off;
         const long long src = (long long)vals[r] - ds.off;
         const float* p = ds.points + src * ds.d;
-        float* o = rows + ds.rows_off + local * ds.p;
+        float v[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-            if (j < ds.p) o[j] = j < ds.d ? __ldg(p + j) : 0.0f;
+        for (int j = 0; j < 8; ++j) v[j] = j < ds.d ? __ldg(p + j) : 0.0f;
+        // rows of every index start on 16 bytes: 8- or 16-byte stores
+        float* o = rows + ds.rows_off + local * ds.p;
+        if (ds.p == 2) {
+            *reinterpret_cast<float2*>(o) = make_float2(v[0], v[1]);
+        } else {
+            reinterpret_cast<float4*>(o)[0] = make_float4(v[0], v[1], v[2], v[3]);
+            if (ds.p == 8) reinterpret_cast<float4*>(o)[1] = make_float4(v[4], v[5], v[6], v[7]);
+        }
         rid[r] = (unsigned int)src;
     }
 }
@@ -489,10 +505,11 @@ knn_status upload(Scratch& sc, const std::vector<T>& host, T** dev, const char* 
     knn_status st = sc.alloc(dev, host.size() ? host.size() : 1, what);
     if (st != KNN_OK) return st;
     if (host.empty()) return KNN_OK;
-    cudaError_t e = cudaMemcpyAsync(*dev, host.data(), host.size() * sizeof(T),
-                                    cudaMemcpyHostToDevice, sc.s);
-    // the host vector may go away before the copy runs: wait for it
-    if (e == cudaSuccess) e = cudaStreamSynchronize(sc.s);
+    // A copy from pageable host memory returns once the source has been
+    // staged (or copied), so the vector may go away right after: no wait,
+    // and no bubble in the stream's work.
+    const cudaError_t e = cudaMemcpyAsync(*dev, host.data(), host.size() * sizeof(T),
+                                          cudaMemcpyHostToDevice, sc.s);
     return e == cudaSuccess ? KNN_OK : cuda_error(e, what);
 }
 
@@ -801,7 +818,12 @@ knn_status batch_build_impl(int count, const float* const* points, const void* c
                 return bail(st);
             b->labels = static_cast<unsigned int*>(gv);
         }
-        batch_gather_kernel<<<grid_blocks(total), 256, 0, s>>>(ddesc, shift, total, sk, sv, b->rows,
+        std::vector<GatherDesc> gdesc(count);
+        for (int i = 0; i < count; ++i)
+            gdesc[i] = GatherDesc{desc[i].points, desc[i].off, desc[i].rows_off, desc[i].d, desc[i].p};
+        GatherDesc* dgd = nullptr;
+        if ((st = upload(sc, gdesc, &dgd, "batch gather descriptors")) != KNN_OK) return bail(st);
+        batch_gather_kernel<<<grid_blocks(total), 256, 0, s>>>(dgd, shift, total, sk, sv, b->rows,
                                                                b->rid);
         count_launches(1);
         if (any_labels) {
@@ -952,11 +974,11 @@ knn_status make_plan(const ghn_batch* b, Layout& lay, cudaStream_t s, ghn_plan* 
     // the shared status word after the groups' counters
     p->status = reinterpret_cast<unsigned int*>(p->counters + 2 * ng);
     for (QueryArgs& a : lay.args) a.status = p->status;
+    // pageable sources: each copy returns once its source is staged (no wait)
     cudaError_t e = cudaMemcpyAsync(dargs, lay.args.data(), lay.args.size() * sizeof(QueryArgs),
                                     cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(dqoff, lay.qoff.data(), lay.qoff.size() * 8, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_error(e, "batch query arguments");
     unsigned long long hoff = 0ull;
     for (size_t g = 0; g < ng; ++g) {
@@ -1214,6 +1236,12 @@ knn_status knn_batch_plan(const ghn_batch* batch, const float* const* queries, c
     }
     if (st == KNN_OK) st = make_plan(batch, lay, cs, p);
     if (st == KNN_OK) {
+        // the arguments must be on the device before any replay, which may
+        // run on another stream
+        const cudaError_t e = cudaStreamSynchronize(cs);
+        if (e != cudaSuccess) st = cuda_error(e, "knn_batch_plan: arguments");
+    }
+    if (st == KNN_OK) {
         // capture the launches once; knn_batch_run replays them
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
@@ -1251,6 +1279,17 @@ knn_status knn_batch_run(ghn_plan* plan, int32_t flags, void* stream)
 }
 
 void knn_plan_free(ghn_plan* plan) { free_plan(plan); }
+
+knn_status knn_batch_set_deferral(ghn_batch* batch, int32_t i, int64_t heavy_rows,
+                                  int64_t heavy_cands)
+{
+    if (!batch || i < 0 || i >= batch->count)
+        return fail("knn_batch_set_deferral: bad argument", KNN_EINVAL);
+    QueryArgs& a = batch->proto[i];
+    a.heavy_rows = deferral_threshold(heavy_rows, heavy_rows_default(a.g.d));
+    a.heavy_cands = deferral_threshold(heavy_cands, heavy_cands_default());
+    return KNN_OK;
+}
 
 void knn_batch_free(ghn_batch* batch) { free_batch(batch); }
 

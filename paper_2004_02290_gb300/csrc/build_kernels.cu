@@ -801,6 +801,164 @@ __global__ void gather_kernel(const float* __restrict__ pts, long long n,
     }
 }
 
+// ---------------------------------------------------------------------------
+// Small dense build: one block of 1024 threads builds a whole index of at most
+// kSmallMaxN points whose box holds at most kSmallMaxCells cells (ids fit 16
+// bits), with everything between the box and the outputs in shared memory:
+//   - Eq. 1 ids of every point (the arithmetic of cell_keys_kernel);
+//   - a stable LSD radix sort of (id, index) by id, 8-bit digits, one or two
+//     passes.  Warp w ranks the 512 consecutive points w*512 .. w*512+511 in
+//     index order (item j of lane l is point w*512 + 32j + l); a digit-major,
+//     warp-minor scan of the warps' digit counts then places every point, so
+//     points of one cell keep ascending index, as the multi-kernel sort does;
+//   - the training index of every row, the rows gathered in cell order, the
+//     dense table (each cell's first row: the number of rows with a smaller
+//     id, by binary search) and the occupied-cell count.
+// The result is the same index as the multi-kernel path builds.
+// ---------------------------------------------------------------------------
+constexpr int kSmallThreads = 1024;
+constexpr int kSmallItems = kSmallMaxN / kSmallThreads;  // points a lane ranks per pass
+static_assert(kSmallMaxN % kSmallThreads == 0, "whole items per lane");
+
+struct SmallSmem {
+    unsigned short key[2][kSmallMaxN];
+    unsigned short idx[2][kSmallMaxN];
+    unsigned int cnt[32][256];  // per warp and digit: counts, then first positions
+    unsigned int wsum[32];
+    unsigned int total;
+};
+
+size_t small_build_smem_bytes() { return sizeof(SmallSmem); }
+
+template <int D>
+__global__ void __launch_bounds__(kSmallThreads, 1)
+    small_build_kernel(const float* __restrict__ pts, int n, GridConst g, unsigned int space,
+                       unsigned int* __restrict__ rid, float* __restrict__ rows,
+                       unsigned int* __restrict__ dstart, GridDev* __restrict__ gdev)
+{
+    extern __shared__ __align__(16) unsigned char small_raw[];
+    SmallSmem& sm = *reinterpret_cast<SmallSmem*>(small_raw);
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const unsigned int lt = (1u << lane) - 1u;
+    constexpr int P = row_floats(D);
+    // ---- Eq. 1 ids ----
+#pragma unroll 4
+    for (int j = 0; j < kSmallItems; ++j) {
+        const int e = w * (32 * kSmallItems) + j * 32 + lane;
+        if (e < n) {
+            unsigned long long key = 0;
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                const float tq =
+                    __fdiv_rn(__fsub_rn(__ldg(pts + (long long)e * D + c), g.lo[c]), g.w[c]);
+                long long cc = (long long)floorf(tq);
+                if (g.split[c] > 0 && cc > g.split[c] - 1) cc = g.split[c] - 1;
+                key += (unsigned long long)cc * g.stride[c];
+            }
+            sm.key[0][e] = (unsigned short)key;
+            sm.idx[0][e] = (unsigned short)e;
+        }
+    }
+    __syncthreads();
+    // ---- stable radix sort by id ----
+    const int passes = space <= 256u ? 1 : 2;
+    int cur = 0;
+    for (int pass = 0; pass < passes; ++pass) {
+        const int sh = 8 * pass;
+        for (int i = t; i < 32 * 256; i += kSmallThreads) (&sm.cnt[0][0])[i] = 0u;
+        __syncthreads();
+        unsigned int rd[kSmallItems];  // digit << 16 | rank within the warp (rank < 2^14)
+#pragma unroll
+        for (int j = 0; j < kSmallItems; ++j) {
+            const int e = w * (32 * kSmallItems) + j * 32 + lane;
+            const bool valid = e < n;
+            const unsigned int d = valid ? ((unsigned int)sm.key[cur][e] >> sh) & 255u : 0u;
+            // the lanes with the same digit (and validity): one ballot per bit
+            unsigned int peers = __ballot_sync(FULL, valid);
+            if (!valid) peers = ~peers;
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const bool bit = (d >> b) & 1u;
+                const unsigned int m = __ballot_sync(FULL, bit);
+                peers &= bit ? m : ~m;
+            }
+            const unsigned int base = valid ? sm.cnt[w][d] : 0u;
+            __syncwarp();
+            if (valid && (peers & lt) == 0u) sm.cnt[w][d] = base + (unsigned int)__popc(peers);
+            __syncwarp();
+            rd[j] = (d << 16) | (base + (unsigned int)__popc(peers & lt));
+        }
+        __syncthreads();
+        {
+            // thread t owns digit t / 4 and warps 8 (t % 4) .. 8 (t % 4) + 7
+            const int d = t >> 2, w0 = (t & 3) * 8;
+            unsigned int sum = 0u;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) sum += sm.cnt[w0 + i][d];
+            unsigned int tot;
+            unsigned int pre = block_scan_incl(sum, sm.wsum, &tot) - sum;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const unsigned int v = sm.cnt[w0 + i][d];
+                sm.cnt[w0 + i][d] = pre;
+                pre += v;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kSmallItems; ++j) {
+            const int e = w * (32 * kSmallItems) + j * 32 + lane;
+            if (e < n) {
+                const unsigned int dst = sm.cnt[w][rd[j] >> 16] + (rd[j] & 0xffffu);
+                sm.key[cur ^ 1][dst] = sm.key[cur][e];
+                sm.idx[cur ^ 1][dst] = sm.idx[cur][e];
+            }
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+    const unsigned short* sk = sm.key[cur];
+    const unsigned short* si = sm.idx[cur];
+    // ---- rows in cell order, their training indices, occupied cells ----
+    unsigned int heads = 0u;
+    for (int r = t; r < n; r += kSmallThreads) {
+        const int i = si[r];
+        rid[r] = (unsigned int)i;
+        float v[P];
+#pragma unroll
+        for (int c = 0; c < P; ++c) v[c] = c < D ? __ldg(pts + (long long)i * D + c) : 0.0f;
+        if constexpr (P == 2) {
+            reinterpret_cast<float2*>(rows)[r] = make_float2(v[0], v[1]);
+        } else {
+#pragma unroll
+            for (int h = 0; h < P / 4; ++h)
+                reinterpret_cast<float4*>(rows)[r * (P / 4) + h] =
+                    make_float4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
+        }
+        heads += (r == 0 || sk[r] != sk[r - 1]) ? 1u : 0u;
+    }
+    // ---- dense table: the first row of cell c is the count of smaller ids ----
+    for (unsigned int c = (unsigned int)t; c <= space; c += kSmallThreads) {
+        int lo = 0, hi = n;  // first row whose id is >= c
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if ((unsigned int)sk[mid] < c)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        dstart[c] = (unsigned int)lo;
+    }
+    unsigned int u;
+    block_scan_incl(heads, sm.wsum, &u);
+    if (t == 0) {
+        unsigned long long cap = 16ull;
+        while (cap < 2ull * u) cap <<= 1;
+        gdev->ncells = u;
+        gdev->hmask = cap - 1ull;
+    }
+}
+
 // Cell id of each query clamped into the box (for the locality order only).
 template <int D, class K>
 __global__ void query_keys_kernel(const float* __restrict__ q, long long m, GridConst g, int shift,
@@ -1145,6 +1303,42 @@ cudaError_t launch_gather(const float* pts, long long n, int d, const unsigned i
     case 8: gather_kernel<8><<<b, 256, 0, s>>>(pts, n, order, rows); break;
     default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_small_build(const float* pts, long long n, int d, const GridConst& g,
+                               unsigned long long space, unsigned int* rid, float* rows,
+                               unsigned int* dstart, GridDev* gdev, cudaStream_t s)
+{
+    if (n < 1 || n > kSmallMaxN || space > kSmallMaxCells) return cudaErrorInvalidValue;
+    const size_t bytes = small_build_smem_bytes();
+    static bool ready[kMaxD + 1] = {false};
+    cudaError_t e = cudaSuccess;
+#define GHN_SMALL_CASE(DD)                                                                      \
+    case DD:                                                                                   \
+        if (!ready[DD]) {                                                                      \
+            e = cudaFuncSetAttribute(small_build_kernel<DD>,                                   \
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); \
+            if (e != cudaSuccess) return e;                                                    \
+            ready[DD] = true;                                                                  \
+        }                                                                                      \
+        small_build_kernel<DD><<<1, kSmallThreads, bytes, s>>>(pts, (int)n, g,                 \
+                                                               (unsigned int)space, rid, rows, \
+                                                               dstart, gdev);                  \
+        break;
+    switch (d) {
+        GHN_SMALL_CASE(1)
+        GHN_SMALL_CASE(2)
+        GHN_SMALL_CASE(3)
+        GHN_SMALL_CASE(4)
+        GHN_SMALL_CASE(5)
+        GHN_SMALL_CASE(6)
+        GHN_SMALL_CASE(7)
+        GHN_SMALL_CASE(8)
+    default: return cudaErrorInvalidValue;
+    }
+#undef GHN_SMALL_CASE
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -71,6 +71,15 @@ cudaError_t launch_bitmap(const unsigned long long* cell_key, const GridDev* gde
 cudaError_t launch_gather(const float* pts, long long n, int d, const unsigned int* order,
                           float* rows, cudaStream_t s);
 
+// Small dense build (one block, shared memory): for n <= kSmallMaxN points in a
+// box of at most kSmallMaxCells cells, the row ids, rows in cell order, dense
+// table (space + 1 entries) and occupied-cell count, in one launch.
+constexpr int kSmallMaxN = 16384;
+constexpr unsigned long long kSmallMaxCells = 32767;
+cudaError_t launch_small_build(const float* pts, long long n, int d, const GridConst& g,
+                               unsigned long long space, unsigned int* rid, float* rows,
+                               unsigned int* dstart, GridDev* gdev, cudaStream_t s);
+
 // Query keys for the locality order: the cell id of each query, clamped into
 // the box, shifted right by `shift` bits (the caller keeps it below 2^32).
 cudaError_t launch_query_keys(const float* q, long long m, const GridConst& g, int shift,

@@ -36,6 +36,10 @@ struct ghn_index {
     unsigned int* bitmap = nullptr;  // hash: occupancy bit per cell of the box, or null
     GridDev* gdev = nullptr;
     cudaEvent_t last_use = nullptr;
+    // deferral to the cooperative kernel (knn_index_set_deferral): 0 = the
+    // library's default, < 0 = never, > 0 = the threshold
+    long long defer_rows = 0;
+    long long defer_cands = 0;
     // filled on first inspection
     bool info_ready = false;
     GridDev host_gdev{};
@@ -102,9 +106,29 @@ unsigned int heavy_rows_env(int d)
     return d <= 4 ? 1024u : 4096u;
 }
 
+// A deferral threshold as the kernels take it: the default, all ones
+// (never), or the value.
+unsigned int deferral(long long set, unsigned int dflt)
+{
+    if (set == 0) return dflt;
+    if (set < 0) return 0xffffffffu;
+    return set > 0xffffffffll ? 0xffffffffu : (unsigned int)set;
+}
+
 unsigned int heavy_cands_env()
 {
     static unsigned int v = env_uint("GHN_HEAVY_CANDS", 8192u);
+    return v;
+}
+
+// The one-launch build of small dense indexes (build_kernels.cu); GHN_SMALL_BUILD=0
+// takes the multi-kernel path for every index (the two give the same index).
+bool small_build_enabled()
+{
+    static const bool v = [] {
+        const char* s = getenv("GHN_SMALL_BUILD");
+        return !(s && s[0] == '0');
+    }();
     return v;
 }
 
@@ -559,6 +583,32 @@ knn_status build_impl(const float* points_user, const void* labels_user, long lo
         }
         x->table = table;
 
+        if (table == KNN_TABLE_DENSE && n <= kSmallMaxN && space <= kSmallMaxCells &&
+            small_build_enabled()) {
+            // ---- small dense index: ids, sort, rows, table in one launch ----
+            st = dalloc(&x->rid, (size_t)n, s, "row ids");
+            if (st == KNN_OK) st = dalloc(&x->gdev, 1, s, "grid");
+            if (st == KNN_OK) st = dalloc(&x->dstart, (size_t)space + 1, s, "dense table");
+            if (st == KNN_OK) st = dalloc(&x->rows, (size_t)n * row_floats(d), s, "rows");
+            if (st == KNN_OK && lab_in) st = dalloc(&x->labels, (size_t)n, s, "labels");
+            if (st != KNN_OK) return fail(st);
+            e = launch_small_build(pts, n, d, g, space, x->rid, x->rows, x->dstart, x->gdev, s);
+            g_timer.mark("small", s);
+            if (e == cudaSuccess && lab_in)
+                e = cudaMemcpyAsync(x->labels, lab_in, (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
+            if (lab_done) {
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(s, lab_done, 0);
+                cudaEventDestroy(lab_done);
+                lab_done = nullptr;
+            }
+            g_timer.mark("gather", s);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x->last_use, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventRecord(x->last_use, s);
+            if (e != cudaSuccess) return fail(cuda_fail(e, "small build"));
+            *out = x;
+            return KNN_OK;
+        }
+
         // ---- Eq. 1 keys, stable sort by cell, cell offsets, table, row gather ----
         // 32-bit keys when every cell id of the box fits (space <= 2^32)
         const bool narrow = bits <= 32;
@@ -770,8 +820,8 @@ knn_status query_impl(const ghn_index* x, const float* queries_user, long long m
         a.heavy_count = reinterpret_cast<unsigned int*>(scratch + 2);
         a.heavy_cursor = reinterpret_cast<unsigned int*>(scratch + 2) + 1;
         a.heavy_list = heavy;
-        a.heavy_rows = heavy_rows_env(x->d);
-        a.heavy_cands = heavy_cands_env();
+        a.heavy_rows = deferral(x->defer_rows, heavy_rows_env(x->d));
+        a.heavy_cands = deferral(x->defer_cands, heavy_cands_env());
         a.stats = stats;
         a.order = order;
         a.max_layers = max_layers_env();
@@ -885,8 +935,8 @@ void index_query_args(const ghn_index* x, QueryArgs& a)
     a.gdev = x->gdev;
     a.max_layers = max_layers_env();
     a.max_rows = max_rows_env();
-    a.heavy_rows = heavy_rows_env(x->d);
-    a.heavy_cands = heavy_cands_env();
+    a.heavy_rows = deferral(x->defer_rows, heavy_rows_env(x->d));
+    a.heavy_cands = deferral(x->defer_cands, heavy_cands_env());
     a.dense = x->table == KNN_TABLE_DENSE;
 }
 
@@ -925,6 +975,7 @@ void device_free(void* p, cudaStream_t s)
 }
 
 unsigned int heavy_rows_default(int d) { return heavy_rows_env(d); }
+unsigned int deferral_threshold(long long set, unsigned int dflt) { return deferral(set, dflt); }
 unsigned int heavy_cands_default() { return heavy_cands_env(); }
 long long max_layers_default() { return max_layers_env(); }
 long long max_rows_default() { return max_rows_env(); }
@@ -1205,6 +1256,17 @@ int32_t knn_timing_read(const char** names, float* ms, int32_t cap)
 }
 
 int64_t knn_kernel_launches(void) { return g_launches.load(); }
+
+knn_status knn_index_set_deferral(ghn_index* index, int64_t heavy_rows, int64_t heavy_cands)
+{
+    if (!index) {
+        set_err("knn_index_set_deferral: index is NULL");
+        return KNN_EINVAL;
+    }
+    index->defer_rows = heavy_rows;
+    index->defer_cands = heavy_cands;
+    return KNN_OK;
+}
 
 void knn_free(ghn_index* index) { free_index(index); }
 

@@ -163,6 +163,8 @@ int device_alloc(void** p, size_t bytes, cudaStream_t s, const char* what);
 void device_free(void* p, cudaStream_t s);
 unsigned int heavy_rows_default(int d);
 unsigned int heavy_cands_default();
+// A per-index deferral setting (0 default, < 0 never, > 0 threshold) as kernels take it.
+unsigned int deferral_threshold(long long set, unsigned int dflt);
 long long max_layers_default();
 long long max_rows_default();
 void tune_device_pool(int dev);

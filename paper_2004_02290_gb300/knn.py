@@ -42,7 +42,7 @@ class knn_index_info_t(ctypes.Structure):
 EXPORTED = ["knn_batch_build", "knn_batch_info", "knn_batch_query", "knn_batch_plan",
             "knn_batch_run", "knn_plan_free", "knn_batch_free",
             "knn_build", "knn_build_grid", "knn_measure_cells", "knn_index_grid", "knn_query", "knn_query_stats", "knn_query_noalloc", "knn_index_info",
-            "knn_index_export",
+            "knn_index_export", "knn_index_set_deferral", "knn_batch_set_deferral",
             "knn_timing_enable", "knn_timing_read", "knn_kernel_launches", "knn_free",
             "knn_last_error", "knn_abi_version",
             "knn_server_create", "knn_server_build", "knn_server_drop", "knn_server_submit",
@@ -104,6 +104,10 @@ def library(path: str | None = None) -> ctypes.CDLL:
         lib.knn_index_info.restype = i32
         lib.knn_index_export.argtypes = [vp, vp, vp, vp]
         lib.knn_index_export.restype = i32
+        lib.knn_index_set_deferral.argtypes = [vp, i64, i64]
+        lib.knn_index_set_deferral.restype = i32
+        lib.knn_batch_set_deferral.argtypes = [vp, i32, i64, i64]
+        lib.knn_batch_set_deferral.restype = i32
         lib.knn_free.argtypes = [vp]
         lib.knn_free.restype = None
         lib.knn_last_error.argtypes = []
@@ -247,6 +251,11 @@ class Index:
 
     def query_stats(self, queries, k: int, stream=None):
         return knn_query_stats(self, queries, k, stream=stream)
+
+    def set_deferral(self, heavy_rows: int = 0, heavy_cands: int = 0):
+        """Thresholds for handing heavy queries to the cooperative kernel
+        (0: library default, < 0: never); results do not depend on them."""
+        _check(library().knn_index_set_deferral(self._h, int(heavy_rows), int(heavy_cands)))
 
     def free(self):
         if self._h is not None and self._h.value:
@@ -404,6 +413,11 @@ class Batch:
         out = knn_index_info_t()
         _check(library().knn_batch_info(self._h, i, ctypes.byref(out)))
         return out
+
+    def set_deferral(self, i: int, heavy_rows: int = 0, heavy_cands: int = 0):
+        """Deferral thresholds of index i (as Index.set_deferral)."""
+        _check(library().knn_batch_set_deferral(self._h, int(i), int(heavy_rows),
+                                                int(heavy_cands)))
 
     def _outputs(self, queries, ks, modes):
         ids, d2, pred = [], [], []

@@ -344,8 +344,8 @@ def test_phase_timing_reads_calls_oldest_first():
         build = knn.knn_timing_read()
         q1 = knn.knn_timing_read()
         q2 = knn.knn_timing_read()
-        assert [n for n, _ in build] == ["stage", "box", "keys", "sort", "cells", "table",
-                                         "gather"]
+        # tiny is a small dense index: one launch builds it ("small")
+        assert [n for n, _ in build] == ["stage", "box", "small", "gather"]
         # search: the warp or slot kernel; coop: the cooperative kernel
         assert [n for n, _ in q1] == [n for n, _ in q2] == ["stage", "order", "search", "coop",
                                                             "copy"]
@@ -429,11 +429,13 @@ def _child(code, env):
                           text=True, timeout=300)
 
 
-def test_injected_allocation_failure():
+@pytest.mark.parametrize("n,ats", [(1000, ("1", "3", "6")),          # one-launch small build
+                                   (40000, ("1", "3", "9", "12"))])  # multi-kernel build
+def test_injected_allocation_failure(n, ats):
     code = (
         "import numpy as np, torch\n"
         "from paper_2004_02290_gb300 import knn, workloads as wl\n"
-        "x, lab, q = wl.uniform(1000, 10, 2, seed=1)\n"
+        f"x, lab, q = wl.uniform({n}, 10, 2, seed=1)\n"
         "try:\n"
         "    knn.knn_build(torch.from_numpy(x).cuda(), torch.from_numpy(lab).cuda(), 0.05)\n"
         "    print('NOFAIL')\n"
@@ -442,11 +444,11 @@ def test_injected_allocation_failure():
         "idx = knn.knn_build(torch.from_numpy(x).cuda(), torch.from_numpy(lab).cuda(), 0.05)\n"
         "ids, _, _ = idx.query(torch.from_numpy(q).cuda(), 3, flags=knn.KNN_QUERY_CHECKED)\n"
         "print('AFTER', int(ids.min()))\n")
-    for at in ("1", "3", "9"):
+    for at in ats:
         r = _child(code, {"GHN_FAIL_ALLOC_AT": at})
         assert r.returncode == 0, r.stderr
-        assert "CODE 2" in r.stdout, r.stdout
-        assert "AFTER 0" in r.stdout or "AFTER" in r.stdout
+        assert "CODE 2" in r.stdout, (at, r.stdout)
+        assert "AFTER 0" in r.stdout, (at, r.stdout)
 
 
 def test_layer_cap_reports_limit():
@@ -526,6 +528,51 @@ def test_buffers_of_another_gpu_are_refused():
         idx.query(q1, 3, knn.KNN_VOTE, flags=knn.KNN_QUERY_CHECKED)
     assert e.value.code == knn.KNN_EINVAL
     idx.free()
+
+
+_BUILD_CASES = r"""
+import sys, numpy as np, torch
+from paper_2004_02290_gb300 import knn, workloads as wl
+def dev(a): return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+out = {}
+cases = [(1, 3000, 0.002), (2, 10000, 0.018), (3, 16384, 0.09), (4, 5000, 0.25), (6, 2000, 0.6),
+         (8, 1500, 0.9), (2, 1, 0.5), (3, 777, 0.05)]
+for ci, (d, n, w) in enumerate(cases):
+    x, lab, q = wl.uniform(n, 200, d, seed=70 + ci)
+    if ci == 1:
+        x, lab, q = wl.make("tiny").points, wl.make("tiny").labels, wl.make("tiny").queries
+    idx = knn.knn_build(dev(x), dev(lab), w, knn.KNN_TABLE_DENSE)
+    inf = idx.info()
+    u = int(inf.num_cells)
+    keys = np.zeros(u, np.uint64); starts = np.zeros(u + 1, np.uint32); rows = np.zeros(len(x), np.int32)
+    lib = knn.library()
+    assert lib.knn_index_export(idx.handle, keys.ctypes.data, starts.ctypes.data, rows.ctypes.data) == 0
+    ids, d2, pred = idx.query(dev(q), 7, knn.KNN_VOTE, flags=knn.KNN_QUERY_CHECKED)
+    torch.cuda.synchronize()
+    out[f"{ci}_k"] = keys; out[f"{ci}_s"] = starts; out[f"{ci}_r"] = rows
+    out[f"{ci}_i"] = ids.cpu().numpy(); out[f"{ci}_d"] = d2.cpu().numpy(); out[f"{ci}_p"] = pred.cpu().numpy()
+    out[f"{ci}_u"] = np.array([u, inf.table], np.int64)
+    idx.free()
+np.savez(sys.argv[1], **out)
+"""
+
+
+def test_small_build_equals_the_multi_kernel_build(tmp_path):
+    """The one-launch build of small dense indexes (n <= 16384, at most 32767
+    cells) and the multi-kernel build (GHN_SMALL_BUILD=0) give the same cell
+    list, row order and query outputs (one point, n = 16384, d = 1..8)."""
+    res = {}
+    for name, env in (("small", {}), ("multi", {"GHN_SMALL_BUILD": "0"})):
+        path = str(tmp_path / f"{name}.npz")
+        r = subprocess.run([sys.executable, "-c", _BUILD_CASES, path], cwd=ROOT,
+                           env=dict(os.environ, **env), capture_output=True, text=True,
+                           timeout=300)
+        assert r.returncode == 0, r.stderr[-3000:]
+        res[name] = np.load(path)
+    a, b = res["small"], res["multi"]
+    assert sorted(a.files) == sorted(b.files)
+    for f in a.files:
+        assert np.array_equal(a[f].view(np.uint8), b[f].view(np.uint8)), f
 
 
 # ---- full-size workloads, in the benchmark's launch configuration, sampled ----
