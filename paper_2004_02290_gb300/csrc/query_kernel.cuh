@@ -555,6 +555,25 @@ __device__ __forceinline__ void row_ranges(const QueryArgs& a, unsigned long lon
         x0b = x0b > c0 ? x0b : c0;
         x1b = x1b < c1 ? x1b : c1;
     }
+#ifdef GHN_RUNS_LOOP
+    // the two runs by one copy of the lookup code
+#pragma unroll 1
+    for (int r = 0; r < 2; ++r) {
+        const long long x0 = r ? x0b : x0a, x1 = r ? x1b : x1a;
+        unsigned int st = 0u, ln = 0u;
+        if (x0 <= x1 &&
+            !(prune && (og2 + axis_gap2((int)x0, (int)x1, s.u[dl], a.g.w[dl])) * (1.0f - 1e-5f) >
+                           kth_d))
+            resolve_run<DENSE>(a, hmask, base, x0, x1, counting, st, ln, cells);
+        if (r) {
+            sb = st;
+            lb = ln;
+        } else {
+            sa = st;
+            la = ln;
+        }
+    }
+#else
     if (x0a <= x1a &&
         !(prune && (og2 + axis_gap2((int)x0a, (int)x1a, s.u[dl], a.g.w[dl])) * (1.0f - 1e-5f) >
                        kth_d))
@@ -563,6 +582,7 @@ __device__ __forceinline__ void row_ranges(const QueryArgs& a, unsigned long lon
         !(prune && (og2 + axis_gap2((int)x0b, (int)x1b, s.u[dl], a.g.w[dl])) * (1.0f - 1e-5f) >
                        kth_d))
         resolve_run<DENSE>(a, hmask, base, x0b, x1b, counting, sb, lb, cells);
+#endif
     if (la == 0u) {
         sa = sb;
         la = lb;
@@ -592,9 +612,14 @@ __device__ __forceinline__ bool offer(TopK<NS>& tk, unsigned long long key, int 
     return true;
 }
 
+#ifdef GHN_OUTPUTS_NOINLINE
+#define GHN_OUTPUTS_INLINE __noinline__
+#else
+#define GHN_OUTPUTS_INLINE __forceinline__
+#endif
 // ids, squared distances and the prediction of one query, from its buffer.
 template <int NS>
-__device__ __forceinline__ void write_outputs(const QueryArgs& a, long long qid,
+__device__ GHN_OUTPUTS_INLINE void write_outputs(const QueryArgs& a, long long qid,
                                               const TopK<NS>& tk, bool limited, int lane)
 {
     const long long obase = qid * (long long)a.k;
