@@ -555,8 +555,8 @@ __device__ __forceinline__ void row_ranges(const QueryArgs& a, unsigned long lon
         x0b = x0b > c0 ? x0b : c0;
         x1b = x1b < c1 ? x1b : c1;
     }
-#ifdef GHN_RUNS_LOOP
-    // the two runs by one copy of the lookup code
+    // the two runs by one copy of the lookup code (a smaller kernel: measured
+    // 5% faster on large_cls than two inlined copies)
 #pragma unroll 1
     for (int r = 0; r < 2; ++r) {
         const long long x0 = r ? x0b : x0a, x1 = r ? x1b : x1a;
@@ -573,22 +573,16 @@ __device__ __forceinline__ void row_ranges(const QueryArgs& a, unsigned long lon
             la = ln;
         }
     }
-#else
-    if (x0a <= x1a &&
-        !(prune && (og2 + axis_gap2((int)x0a, (int)x1a, s.u[dl], a.g.w[dl])) * (1.0f - 1e-5f) >
-                       kth_d))
-        resolve_run<DENSE>(a, hmask, base, x0a, x1a, counting, sa, la, cells);
-    if (x0b <= x1b &&
-        !(prune && (og2 + axis_gap2((int)x0b, (int)x1b, s.u[dl], a.g.w[dl])) * (1.0f - 1e-5f) >
-                       kth_d))
-        resolve_run<DENSE>(a, hmask, base, x0b, x1b, counting, sb, lb, cells);
-#endif
     if (la == 0u) {
         sa = sb;
         la = lb;
         lb = 0u;
     }
 }
+
+// Above this many entering keys, one bitonic merge is cheaper than inserting
+// the keys one by one (4 measured 1-2% slower on GB300).
+constexpr int kMergeMin = 6;
 
 // Offer one key per lane to the buffer; true when some key entered it.  Keys
 // not below `cap` are refused (the cooperative kernel's block-wide k-th key).
@@ -599,7 +593,7 @@ __device__ __forceinline__ bool offer(TopK<NS>& tk, unsigned long long key, int 
     const bool pass = key < (tk.kth < cap ? tk.kth : cap);
     unsigned int pm = __ballot_sync(FULL, pass);
     if (pm == 0u) return false;
-    if (NS == 1 && __popc(pm) > 6) {
+    if (NS == 1 && __popc(pm) > kMergeMin) {
         tk.merge32(pass ? key : kEmptyKey, lane);
     } else {
         while (pm) {
@@ -612,14 +606,9 @@ __device__ __forceinline__ bool offer(TopK<NS>& tk, unsigned long long key, int 
     return true;
 }
 
-#ifdef GHN_OUTPUTS_NOINLINE
-#define GHN_OUTPUTS_INLINE __noinline__
-#else
-#define GHN_OUTPUTS_INLINE __forceinline__
-#endif
 // ids, squared distances and the prediction of one query, from its buffer.
 template <int NS>
-__device__ GHN_OUTPUTS_INLINE void write_outputs(const QueryArgs& a, long long qid,
+__device__ __forceinline__ void write_outputs(const QueryArgs& a, long long qid,
                                               const TopK<NS>& tk, bool limited, int lane)
 {
     const long long obase = qid * (long long)a.k;
@@ -757,14 +746,12 @@ __device__ GHN_OUTPUTS_INLINE void write_outputs(const QueryArgs& a, long long q
 // Resident blocks per SM the warp kernel is compiled for.  The walk is bound by
 // memory latency and instruction issue, so more resident warps pay even when
 // the register cap spills a little to L1 (measured: 8 blocks on the d=3 and
-// d=4 workloads; 6 for d=5 and 6, 3% faster than 4 on the heaviest d=6
-// problems; 4 for the larger query state of d=7 and 8).
-#ifndef GHN_MIN_BLOCKS_D4
-#define GHN_MIN_BLOCKS_D4 8
-#endif
+// d=4 workloads, where 6 was 3% slower; 6 for d=5 and 6, 3% faster than 4
+// and 52% faster than 8 on the batched d=6 problems; 4 for the larger query
+// state of d=7 and 8).
 template <int D, int NS>
 struct MinBlocks {
-    static constexpr int value = NS == 1 ? (D <= 4 ? GHN_MIN_BLOCKS_D4 : (D <= 6 ? 6 : 4)) : 2;
+    static constexpr int value = NS == 1 ? (D <= 4 ? 8 : (D <= 6 ? 6 : 4)) : 2;
 };
 
 // Per-warp shared memory of the walk: the lanes' ranges of one row batch.
