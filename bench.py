@@ -268,8 +268,10 @@ def run_reference_batched(args):
     desc = (f"each step: the same {len(sample)} of {len(ps)} problems, whole (build + all "
             f"{q} of their queries, {cores} threads over queries); widths: the autotuner's "
             f"starting guess")
-    config = {"workload": "batched", "problems": len(ps), "sample_problems": len(sample),
-              "sample_queries": int(q), "queries": int(sum(p_.m for p_ in ps))}
+    config = {"workload": "batched", "problems": len(ps),
+              "points": int(sum(p_.n for p_ in ps)), "queries": int(sum(p_.m for p_ in ps)),
+              "dims": sorted({p_.d for p_ in ps}), "ks": sorted({p_.k for p_ in ps}),
+              "sample_problems": len(sample), "sample_queries": int(q)}
     print(json.dumps(_reference_line(args, METRIC_BATCHED, value, steps, config, desc, cores)),
           flush=True)
 
@@ -1052,6 +1054,9 @@ def run_profile_case(args):
         pts = [torch.from_numpy(p_.points).to(dev) for p_ in ps]
         lab = [torch.from_numpy(p_.labels).to(dev) for p_ in ps]
         qs = [torch.from_numpy(p_.queries).to(dev) for p_ in ps]
+        while knn.knn_timing_read():  # drop the tuner's calls
+            pass
+        groups = {}
         for _ in range(args.repeat):
             b = knn.knn_batch_build(pts, lab, widths)
             for i, x in enumerate(defer):
@@ -1059,11 +1064,17 @@ def run_profile_case(args):
                     b.set_deferral(i, *x)
             b.query(qs, [p_.k for p_ in ps], [p_.mode for p_ in ps],
                     flags=knn.KNN_QUERY_CHECKED)
+            groups = {}
+            for i, p_ in enumerate(ps):
+                dense = b.info(i).table == knn.KNN_TABLE_DENSE
+                g = f"query.d{p_.d}.{'k64' if p_.k > 32 else 'k32'}.{'dense' if dense else 'hash'}"
+                groups[g] = groups.get(g, 0) + p_.m
             b.free()
             for c in ("build", "query"):
                 print(c + ":", knn.knn_timing_read())
         torch.cuda.synchronize()
         print(f"batched: {len(ps)} problems, {sum(p_.m for p_ in ps)} queries")
+        print("queries per group:", json.dumps(dict(sorted(groups.items()))))
         return
     if args.batched_problem is not None:
         if args.width is None:
