@@ -333,6 +333,23 @@ __device__ __forceinline__ void resolve_run(const QueryArgs& a, unsigned long lo
 // Per-query pieces shared by the warp kernel and the cooperative kernel
 // ---------------------------------------------------------------------------
 
+// Squared distance between a query and a stored row, in the order the
+// oracle fixes: per dimension a rounded difference, a rounded square and a
+// rounded running sum (no fused multiply-add).  The sum starts from the first
+// square itself: 0 + x is x for every square x (never -0).
+template <int D, int P>
+__device__ __forceinline__ float sq_dist(const float (&q)[D], const Row<P>& row)
+{
+    const float d0 = __fsub_rn(q[0], row.v[0]);
+    float acc = __fmul_rn(d0, d0);
+#pragma unroll
+    for (int j = 1; j < D; ++j) {
+        const float dj = __fsub_rn(q[j], row.v[j]);
+        acc = __fadd_rn(acc, __fmul_rn(dj, dj));
+    }
+    return acc;
+}
+
 template <int D>
 struct Query {
     float q[D];
@@ -755,12 +772,14 @@ struct MinBlocks {
 };
 
 // Per-warp shared memory of the walk: the lanes' ranges of one row batch.
+// Lane l's candidates are the flattened positions t in [end[l-1], end[l]):
+// its first range for t < mid[l], its second one after, and the stored row
+// of t is ao[l] + t or bo[l] + t (offsets taken modulo 2^32).
 struct WarpSmem {
     unsigned int end[32];  // inclusive end of each lane's ranges, flattened
-    unsigned int beg[32];  // exclusive start of each lane's ranges
-    unsigned int a[32];    // first range: start
-    unsigned int la[32];   // first range: length
-    unsigned int b[32];    // second range: start
+    unsigned int mid[32];  // where the lane's second range starts, flattened
+    unsigned int ao[32];   // first range: row of t minus t
+    unsigned int bo[32];   // second range: row of t minus t
 };
 
 // The lane whose ranges hold flattened candidate t (t < end[31]): binary
@@ -843,10 +862,9 @@ __device__ __forceinline__ bool walk_query(const QueryArgs& a, long long qid, Wa
                 }
                 __syncwarp();
                 sm.end[lane] = incl;
-                sm.beg[lane] = incl - tot;
-                sm.a[lane] = sa;
-                sm.la[lane] = la;
-                sm.b[lane] = sb;
+                sm.mid[lane] = incl - lb;
+                sm.ao[lane] = sa - (incl - tot);
+                sm.bo[lane] = sb - (incl - lb);
                 __syncwarp();
                 // chunks of 32 candidates; the next chunk's rows are loaded
                 // while the current one is offered to the buffer
@@ -854,19 +872,18 @@ __device__ __forceinline__ bool walk_query(const QueryArgs& a, long long qid, Wa
                 // each lane's cursor: the lane `own` whose ranges hold its
                 // next candidate (a binary search for the first chunk, then
                 // forward moves only when a chunk step leaves own's ranges)
-                // and a copy of own's ranges
-                unsigned int own = 0u, o_end = 0u, o_beg = 0u, o_la = 0u, o_a = 0u, o_b = 0u;
+                // and a copy of own's range offsets
+                unsigned int own = 0u, o_end = 0u, o_mid = 0u, o_ao = 0u, o_bo = 0u;
                 Row<P> nrow;
                 unsigned int npos = 0u;
                 if (lane < total) {
                     own = owner_of(sm.end, lane);
                     o_end = sm.end[own];
-                    o_beg = sm.beg[own];
-                    o_la = sm.la[own];
-                    o_a = sm.a[own];
-                    o_b = sm.b[own];
-                    const unsigned int off = (unsigned int)lane - o_beg;
-                    npos = off < o_la ? o_a + off : o_b + (off - o_la);
+                    o_mid = sm.mid[own];
+                    o_ao = sm.ao[own];
+                    o_bo = sm.bo[own];
+                    const unsigned int t0 = (unsigned int)lane;
+                    npos = (t0 < o_mid ? o_ao : o_bo) + t0;
                     nrow.load(a.rows, npos);
                 }
                 // the k-th squared distance (+inf while the buffer is short)
@@ -882,23 +899,17 @@ __device__ __forceinline__ bool walk_query(const QueryArgs& a, long long qid, Wa
                                 ++own;
                             } while (sm.end[own] <= tn);  // ends at 31 at the latest
                             o_end = sm.end[own];
-                            o_beg = sm.beg[own];
-                            o_la = sm.la[own];
-                            o_a = sm.a[own];
-                            o_b = sm.b[own];
+                            o_mid = sm.mid[own];
+                            o_ao = sm.ao[own];
+                            o_bo = sm.bo[own];
                         }
-                        const unsigned int off = tn - o_beg;
-                        npos = off < o_la ? o_a + off : o_b + (off - o_la);
+                        npos = (tn < o_mid ? o_ao : o_bo) + tn;
                         nrow.load(a.rows, npos);
                     }
                     bool pass = false;
                     float acc = 0.0f;
                     if (t < total) {
-#pragma unroll
-                        for (int j = 0; j < D; ++j) {
-                            const float dj = __fsub_rn(s.q[j], row.v[j]);
-                            acc = __fadd_rn(acc, __fmul_rn(dj, dj));
-                        }
+                        acc = sq_dist<D, P>(s.q, row);
                         pass = acc <= kf;
                     }
                     // the training index is read only for the candidates that
@@ -1122,11 +1133,7 @@ __device__ __forceinline__ void coop_query(const QueryArgs& a, long long qid, Co
                         constexpr int P = row_floats(D);
                         Row<P> row;
                         row.load(a.rows, pos);
-#pragma unroll
-                        for (int j = 0; j < D; ++j) {
-                            const float dj = __fsub_rn(s.q[j], row.v[j]);
-                            acc = __fadd_rn(acc, __fmul_rn(dj, dj));
-                        }
+                        acc = sq_dist<D, P>(s.q, row);
                         const unsigned long long ek2 = tk.kth < gkth ? tk.kth : gkth;
                         pass = ek2 == kEmptyKey || acc <= __uint_as_float((unsigned)(ek2 >> 32));
                     }
