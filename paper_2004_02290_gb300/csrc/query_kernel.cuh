@@ -999,19 +999,27 @@ __global__ void __launch_bounds__(kThreads, (MinBlocks<D, NS>::value))
 // "updated" it exactly when it changed, so the stop rule is the one of the
 // sequential walk.  A warp skips with min(its own k-th key, the block's),
 // which is never below the merged k-th key.
+//
+// A deferred query is a latency chain: its layers, and the rounds of rows
+// within a layer, run one after another, while few queries are deferred at
+// a time.  The block is 512 threads, the widest that keeps the walk's
+// registers (about 128 a thread) without spilling, so a round resolves 512
+// rows.
 // ---------------------------------------------------------------------------
 
-constexpr int kRoundRows = kThreads;      // rows resolved per round (one per thread)
+constexpr int kCoopWarps = 16;
+constexpr int kCoopThreads = kCoopWarps * 32;
+constexpr int kRoundRows = kCoopThreads;  // rows resolved per round (one per thread)
 constexpr int kRangeCap = 2 * kRoundRows;  // at most two ranges per row
 
 // Shared memory of the cooperative walk.
 struct CoopSmem {
     unsigned long long top[64];        // the block's buffer
-    unsigned long long loc[kWarps][64];  // each warp's list of the layer
+    unsigned long long loc[kCoopWarps][64];  // each warp's list of the layer
     unsigned int r_start[kRangeCap];
     unsigned int r_len[kRangeCap];
     unsigned int r_end[kRangeCap];  // inclusive end of each range, flattened
-    unsigned int wsum[kWarps];
+    unsigned int wsum[kCoopWarps];
     unsigned int nr;
     int count;
     int updated;
@@ -1106,12 +1114,12 @@ __device__ __forceinline__ void coop_query(const QueryArgs& a, long long qid, Co
                 if (i0 < nr) sm.r_end[i0] = x - v1;
                 if (i1 < nr) sm.r_end[i1] = x;
                 unsigned int total = 0u;
-                for (int w2 = 0; w2 < kWarps; ++w2) total += sm.wsum[w2];
+                for (int w2 = 0; w2 < kCoopWarps; ++w2) total += sm.wsum[w2];
                 __syncthreads();
                 // the candidates, 32 per warp at a time; each thread keeps the
                 // range of its last candidate and searches forward from it
                 unsigned int r_own = 0u;
-                for (unsigned int cb = 32u * wib; cb < total; cb += 32u * kWarps) {
+                for (unsigned int cb = 32u * wib; cb < total; cb += 32u * kCoopWarps) {
                     const unsigned int t = cb + lane;
                     bool pass = false;
                     float acc = 0.0f;
@@ -1161,7 +1169,8 @@ __device__ __forceinline__ void coop_query(const QueryArgs& a, long long qid, Co
             for (int i = 0; i < NS; ++i) g.s[i] = sm.top[i * 32 + lane];
             g.count = sm.count;
             g.refresh_kth();
-            for (int w2 = 0; w2 < kWarps; ++w2) {
+            for (int w2 = 0; w2 < kCoopWarps; ++w2) {
+                if (!(sm.loc[w2][0] < g.kth)) continue;  // sorted: nothing enters
                 if constexpr (NS == 1) {
                     g.merge32(sm.loc[w2][lane], lane);
                 } else {
@@ -1214,7 +1223,7 @@ __device__ __forceinline__ void coop_query(const QueryArgs& a, long long qid, Co
 }
 
 template <int D, int NS, bool DENSE, bool EXACT>
-__global__ void __launch_bounds__(kThreads, 1) heavy_kernel(const QueryArgs a)
+__global__ void __launch_bounds__(kCoopThreads, 1) heavy_kernel(const QueryArgs a)
 {
     __shared__ CoopSmem sm;
     __shared__ unsigned int s_h;
@@ -1278,7 +1287,7 @@ __global__ void __launch_bounds__(kThreads, (MinBlocks<D, NS>::value))
 }
 
 template <int D, int NS, bool DENSE, bool EXACT>
-__global__ void __launch_bounds__(kThreads, 1) batch_heavy_kernel(const BatchArgs g)
+__global__ void __launch_bounds__(kCoopThreads, 1) batch_heavy_kernel(const BatchArgs g)
 {
     __shared__ CoopSmem sm;
     __shared__ unsigned int s_h;
@@ -1324,10 +1333,11 @@ cudaError_t launch_one(const QueryArgs& a, int sms, cudaStream_t s)
     kernel_mark("search", s);
     if (e != cudaSuccess || a.heavy_list == nullptr || COUNT) return e;
     long long hb =
-        (long long)sms * blocks_per_sm(heavy_kernel<D, NS, DENSE, EXACT>, per_sm_heavy);
+        (long long)sms *
+        blocks_per_sm(heavy_kernel<D, NS, DENSE, EXACT>, per_sm_heavy, kCoopThreads);
     if (hb > a.m) hb = a.m;
     if (hb < 1) hb = 1;
-    heavy_kernel<D, NS, DENSE, EXACT><<<(int)hb, kThreads, 0, s>>>(a);
+    heavy_kernel<D, NS, DENSE, EXACT><<<(int)hb, kCoopThreads, 0, s>>>(a);
     count_launches(1);
     kernel_mark("coop", s);
     return cudaGetLastError();
@@ -1347,10 +1357,11 @@ cudaError_t launch_batch_one(const BatchArgs& g, int sms, cudaStream_t s)
     kernel_mark(group_phase_name(D, NS, DENSE, EXACT, false), s);
     if (e != cudaSuccess || g.heavy_list == nullptr) return e;
     long long hb =
-        (long long)sms * blocks_per_sm(batch_heavy_kernel<D, NS, DENSE, EXACT>, per_sm_heavy);
+        (long long)sms *
+        blocks_per_sm(batch_heavy_kernel<D, NS, DENSE, EXACT>, per_sm_heavy, kCoopThreads);
     if (hb > (long long)g.total) hb = (long long)g.total;
     if (hb < 1) hb = 1;
-    batch_heavy_kernel<D, NS, DENSE, EXACT><<<(int)hb, kThreads, 0, s>>>(g);
+    batch_heavy_kernel<D, NS, DENSE, EXACT><<<(int)hb, kCoopThreads, 0, s>>>(g);
     count_launches(1);
     kernel_mark(group_phase_name(D, NS, DENSE, EXACT, true), s);
     return cudaGetLastError();
