@@ -179,6 +179,17 @@ struct TopK {
     }
 };
 
+// An upper bound of the exact square of a distance whose rounded square is at
+// most x, for the roots that turn a squared distance into a radius.  A normal
+// square is rounded by at most half an ulp, far inside the margins taken with
+// the roots; a subnormal one by up to half the subnormal step 2^-149, which
+// can be half of x itself, so one step is added.  The bound is at least the
+// smallest normal number: the approximate root never sees a subnormal.
+__device__ __forceinline__ float square_bound(float x)
+{
+    return fmaxf(x + 1.4e-45f, 1.17549435e-38f);
+}
+
 // Margin for the rounding of Eq. 1 and of float conversions (cell units).
 __device__ __forceinline__ float axis_margin(float c, float u)
 {
@@ -334,19 +345,33 @@ __device__ __forceinline__ void resolve_run(const QueryArgs& a, unsigned long lo
 // ---------------------------------------------------------------------------
 
 // Squared distance between a query and a stored row, in the order the
-// oracle fixes: per dimension a rounded difference, a rounded square and a
-// rounded running sum (no fused multiply-add).  The sum starts from the first
-// square itself: 0 + x is x for every square x (never -0).
+// oracle fixes: per dimension a rounded difference and a rounded square, then
+// a rounded running sum over the dimensions in order (no fused multiply-add).
+// The differences and squares of two dimensions are computed together by the
+// packed single-precision instructions (sub/mul .rn.f32x2: each half rounded
+// to nearest as the scalar instruction is, subnormals kept); the sum stays one
+// scalar chain.  It starts from the first square itself: 0 + x is x for
+// every square x (never -0).
 template <int D, int P>
 __device__ __forceinline__ float sq_dist(const float (&q)[D], const Row<P>& row)
 {
-    const float d0 = __fsub_rn(q[0], row.v[0]);
-    float acc = __fmul_rn(d0, d0);
+    float sq[D];
 #pragma unroll
-    for (int j = 1; j < D; ++j) {
-        const float dj = __fsub_rn(q[j], row.v[j]);
-        acc = __fadd_rn(acc, __fmul_rn(dj, dj));
+    for (int j = 0; j + 1 < D; j += 2) {
+        unsigned long long qq, xx, dd, ss;
+        asm("mov.b64 %0, {%1, %2};" : "=l"(qq) : "f"(q[j]), "f"(q[j + 1]));
+        asm("mov.b64 %0, {%1, %2};" : "=l"(xx) : "f"(row.v[j]), "f"(row.v[j + 1]));
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dd) : "l"(qq), "l"(xx));
+        asm("mul.rn.f32x2 %0, %1, %1;" : "=l"(ss) : "l"(dd));
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(sq[j]), "=f"(sq[j + 1]) : "l"(ss));
     }
+    if constexpr (D % 2 == 1) {
+        const float dl = __fsub_rn(q[D - 1], row.v[D - 1]);
+        sq[D - 1] = __fmul_rn(dl, dl);
+    }
+    float acc = sq[0];
+#pragma unroll
+    for (int j = 1; j < D; ++j) acc = __fadd_rn(acc, sq[j]);
     return acc;
 }
 
@@ -406,9 +431,10 @@ __device__ __forceinline__ void layer_box(const QueryArgs& a, const Query<D>& s,
     }
     if (!skipping) return;
     // a cell farther than kd along one axis cannot hold a point that enters;
-    // the radius r_j = sqrt(kd) / w_j in cell units is taken with fast
-    // approximate operations (errors near 1e-6) and widened by 1e-4
-    const float rk = (kd > 0.0f ? kd * rsqrtf(kd) : 0.0f) * (1.0f + 1e-4f);
+    // the radius r_j = sqrt(kd) / w_j in cell units is taken of square_bound(kd)
+    // with fast approximate operations (errors near 1e-6) and widened by 1e-4
+    const float kb = square_bound(kd);
+    const float rk = kb * rsqrtf(kb) * (1.0f + 1e-4f);
     bool shell = false;
 #pragma unroll
     for (int j = 0; j < D; ++j) {
@@ -556,11 +582,13 @@ __device__ __forceinline__ void row_ranges(const QueryArgs& a, unsigned long lon
     if (prune && kth_d <= 3.0e38f) {
         // along the row's own axis only the cells within the radius left over
         // by the outer axes, sqrt(kth_d - og2), can hold a point that enters:
-        // clip both runs to them (approximate root, widened as in layer_box).
+        // clip both runs to them (the root of square_bound, approximate and
+        // widened as in layer_box).
         // An infinite k-th distance (overflowed squares) clips nothing.
         const float rem = kth_d * (1.0f + 2e-5f) - og2;
         if (rem < 0.0f) return;
-        const float r = (rem > 0.0f ? rem * rsqrtf(rem) : 0.0f) * a.g.inv_w[dl] * (1.0f + 1e-4f);
+        const float rb = square_bound(rem);
+        const float r = rb * rsqrtf(rb) * a.g.inv_w[dl] * (1.0f + 1e-4f);
         const float u = s.u[dl];
         const float m = 1e-5f * (fabsf(u) + r) + 1e-3f;
         const float c0f = floorf(u - r - m), c1f = floorf(u + r + m);

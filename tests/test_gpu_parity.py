@@ -184,6 +184,23 @@ def test_single_cell_and_duplicates():
         assert_same(got, oracle_run(x, lab, q, 5.0, 20, knn.KNN_VOTE), knn.KNN_VOTE)
 
 
+@pytest.mark.parametrize("d", [2, 3, 5, 6])
+@pytest.mark.parametrize("scale", [1e-20, 1e-21])
+def test_subnormal_squared_distances(d, scale):
+    """Coordinates near 1e-20: every squared difference is subnormal, so a
+    flush to zero anywhere in the distance arithmetic (squares or sums)
+    changes distance bits or the order of the neighbours."""
+    x, lab, q = wl.uniform(3000, 200, d, seed=40 + d)
+    x = (x * np.float32(scale)).astype(np.float32)
+    q = (q * np.float32(scale)).astype(np.float32)
+    w = float(np.float32(scale / 5))
+    exp = oracle_run(x, lab, q, w, 8, knn.KNN_VOTE)
+    assert (exp[1][exp[1] > 0] < np.float32(1.17549435e-38)).all()  # subnormal range
+    for table in (knn.KNN_TABLE_DENSE, knn.KNN_TABLE_HASH):
+        got, _ = gpu_run(x, lab, q, w, 8, knn.KNN_VOTE, table)
+        assert_same(got, exp, knn.KNN_VOTE)
+
+
 def test_k_larger_than_n():
     x, lab, q = wl.uniform(11, 40, 2, seed=8)
     for k in (11, 12, 64):
