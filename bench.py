@@ -400,13 +400,19 @@ def measured_peaks():
 QUERY_SOURCES = ("query_kernel.cuh", "ghn_internal.cuh")
 
 
-def query_kernel_sha() -> str:
-    """Hash of the query kernels' source: a profile summary is used only while it matches."""
+def kernel_sha(files=QUERY_SOURCES) -> str:
+    """Hash of kernel source files (under the package's csrc/): a profile
+    summary is used only while it matches."""
     h = hashlib.sha256()
-    for f in QUERY_SOURCES:
+    for f in files:
         with open(os.path.join(ROOT, "paper_2004_02290_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def query_kernel_sha() -> str:
+    """Hash of the query kernels' source."""
+    return kernel_sha(QUERY_SOURCES)
 
 
 def _field(text, name):
@@ -419,14 +425,21 @@ def profiled(workload: str, phase: str):
     ncu summaries (profiles/*_ncu.md), if taken on the current kernel source.
 
     A summary names its workload, phase and source hash in `key: value`
-    lines, and gives dram_bytes_per_launch (a full-size launch) and, from a
-    full-set capture, issue_active_pct and warp_inst_per_query."""
-    sha = query_kernel_sha()
+    lines (the hash of the files in `kernel_sources`, comma-separated, else
+    of the query kernels' source), and gives dram_bytes_per_launch (a
+    full-size launch) and, from a full-set capture, issue_active_pct and
+    warp_inst_per_query."""
     for path in sorted(glob.glob(os.path.join(PROFILES, "*_ncu.md"))):
         with open(path) as f:
             text = f.read()
-        if (_field(text, "workload") != workload or _field(text, "phase") != phase
-                or _field(text, "kernel_source_sha256_16") != sha):
+        if _field(text, "workload") != workload or _field(text, "phase") != phase:
+            continue
+        files = _field(text, "kernel_sources")
+        try:
+            sha = kernel_sha(tuple(files.split(","))) if files else query_kernel_sha()
+        except OSError:
+            continue
+        if _field(text, "kernel_source_sha256_16") != sha:
             continue
         out = {"summary": os.path.relpath(path, ROOT), "bound": _field(text, "bound")}
         for k in ("dram_bytes_per_launch", "issue_active_pct", "warp_inst_per_query"):

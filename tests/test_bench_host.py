@@ -89,6 +89,19 @@ def test_profiled_ignores_stale_summaries(tmp_path, monkeypatch):
     assert bench.profiled("large_cls", "query.coop") is None     # another kernel
 
 
+def test_profiled_build_kernel_summary_keys_on_its_own_source(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "PROFILES", str(tmp_path))
+    p = tmp_path / "s_tiny_ncu.md"
+    p.write_text(_summary("tiny", "build.small", bench.query_kernel_sha(),
+                          extra="kernel_sources: build_kernels.cu\n"))
+    assert bench.profiled("tiny", "build.small") is None  # the query source's hash
+    p.write_text(_summary("tiny", "build.small", bench.kernel_sha(("build_kernels.cu",)),
+                          dram=5e5, extra="kernel_sources: build_kernels.cu\n"))
+    assert bench.profiled("tiny", "build.small")["dram_bytes_per_launch"] == 5e5
+    p.write_text(_summary("tiny", "build.small", "0000", extra="kernel_sources: nofile.cu\n"))
+    assert bench.profiled("tiny", "build.small") is None
+
+
 def test_roofline_uses_measured_traffic_and_issue_rate(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "PROFILES", str(tmp_path))
     (tmp_path / "b_ncu.md").write_text(_summary(

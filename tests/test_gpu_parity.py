@@ -201,6 +201,22 @@ def test_subnormal_squared_distances(d, scale):
         assert_same(got, exp, knn.KNN_VOTE)
 
 
+@pytest.mark.parametrize("d,scale", [(2, 1e21), (4, 1.5e20), (5, 1e20)])
+def test_overflowing_squared_distances(d, scale):
+    """Coordinates near 1e20: most neighbours' squared distances overflow to
+    +inf, so keys tie on the distance and the training index orders them,
+    and the k-th distance is often infinite (no skipping)."""
+    x, lab, q = wl.uniform(3000, 200, d, seed=50 + d)
+    x = (x * np.float32(scale)).astype(np.float32)
+    q = (q * np.float32(scale)).astype(np.float32)
+    w = float(np.float32(scale / 8))
+    exp = oracle_run(x, lab, q, w, 8, knn.KNN_VOTE)
+    assert np.isinf(exp[1]).any() and np.isfinite(exp[1]).any()
+    for table in (knn.KNN_TABLE_DENSE, knn.KNN_TABLE_HASH):
+        got, _ = gpu_run(x, lab, q, w, 8, knn.KNN_VOTE, table)
+        assert_same(got, exp, knn.KNN_VOTE)
+
+
 def test_k_larger_than_n():
     x, lab, q = wl.uniform(11, 40, 2, seed=8)
     for k in (11, 12, 64):
