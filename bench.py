@@ -174,23 +174,39 @@ def oracle_problem(p_, width, cores, keep=False):
     return sec, out
 
 
-def oracle_problems(problems, widths, budget_s: float = 15.0, keep=False):
+# the batched reference arm draws its sample from problems of at most this
+# many points, so that one step stays near --ref-step-seconds
+REF_N_CAP = 300_000
+
+
+def oracle_problems(problems, widths, budget_s: float = 15.0, keep=False, max_one_s=None,
+                    n_cap=None):
     """The oracle on whole problems in a fixed sample order until about
-    budget_s has been spent.
+    budget_s has been spent.  Problems of more than n_cap points are passed
+    over.  With max_one_s, a problem that alone takes longer is left out of
+    the sample (and selection stops after 4 × budget_s of trying), so that a
+    step over the sample stays near budget_s.
 
     Returns (queries per second over the problems done, details, outputs by
     problem index when `keep`)."""
     cores = host_cores()
     order = np.random.default_rng(0).permutation(len(problems))
-    spent, qdone, done, outs = 0.0, 0, [], {}
+    spent, qdone, done, outs, tried = 0.0, 0, [], {}, 0.0
     for i in order:
+        if n_cap is not None and problems[i].n > n_cap:
+            continue
         sec, out = oracle_problem(problems[i], widths[i], cores, keep)
+        tried += sec
+        if max_one_s is not None and sec > max_one_s:
+            if tried >= 4 * budget_s:
+                break
+            continue
         spent += sec
         qdone += problems[i].m
         done.append(int(i))
         if keep:
             outs[int(i)] = out
-        if spent >= budget_s:
+        if spent >= budget_s or (max_one_s is not None and tried >= 4 * budget_s):
             break
     return qdone / spent, {"problems": len(done), "of": len(problems), "queries": qdone,
                            "seconds": spent, "cores": cores, "which": done}, outs
@@ -244,15 +260,17 @@ def _reference_line(args, metric, value, step_s, config, sample, cores):
 def run_reference_batched(args):
     """The oracle on the batched workload.  Each step runs the same fixed
     sample of whole problems (build + every query), chosen in the first
-    warm-up step to take about --ref-step-seconds; the line reports the
-    queries of that sample over the time the steps took.  Widths are the
-    autotuner's starting guess (tuning needs the GPU)."""
+    warm-up step to take about --ref-step-seconds (a problem that alone
+    takes longer is left out); the line reports the queries of that sample
+    over the time the steps took.  Widths are the autotuner's starting guess
+    (tuning needs the GPU)."""
     from paper_2004_02290_gb300 import autotune
 
     ps = wl.gen_batched(args.batch_count, seed=3)
     widths = [autotune.start_width(p_.points, p_.k) for p_ in ps]
     cores = host_cores()
-    _, det, _ = oracle_problems(ps, widths, budget_s=args.ref_step_seconds)
+    _, det, _ = oracle_problems(ps, widths, budget_s=args.ref_step_seconds,
+                                max_one_s=args.ref_step_seconds, n_cap=REF_N_CAP)
     sample = det["which"]
     for _ in range(max(0, args.warmup - 1)):
         for i in sample:
@@ -265,9 +283,9 @@ def run_reference_batched(args):
         steps.append(t)
     q = sum(ps[i].m for i in sample)
     value = q * len(steps) / sum(steps)
-    desc = (f"each step: the same {len(sample)} of {len(ps)} problems, whole (build + all "
-            f"{q} of their queries, {cores} threads over queries); widths: the autotuner's "
-            f"starting guess")
+    desc = (f"each step: the same {len(sample)} of {len(ps)} problems (drawn from those of at "
+            f"most {REF_N_CAP} points), whole (build + all {q} of their queries, {cores} "
+            f"threads over queries); widths: the autotuner's starting guess")
     config = {"workload": "batched", "problems": len(ps),
               "points": int(sum(p_.n for p_ in ps)), "queries": int(sum(p_.m for p_ in ps)),
               "dims": sorted({p_.d for p_ in ps}), "ks": sorted({p_.k for p_ in ps}),
