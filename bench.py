@@ -801,6 +801,11 @@ def batched_widths(ps, args, dev):
         return [float(x) for x in saved["widths"]], 0.0, None, defer
     widths, tune_s, choices = autotune.tune_batch(ps, dev=dev)
     defer = [tuple(c.deferral) for c in choices]
+    defer, refine_s, groups = autotune.refine_batch_deferral(ps, widths, defer, dev=dev)
+    tune_s += refine_s
+    for c, x in zip(choices, defer):
+        c.deferral = x
+    args.group_deferral = groups
     if args.widths_out:
         os.makedirs(os.path.dirname(os.path.abspath(args.widths_out)), exist_ok=True)
         with open(args.widths_out, "w") as f:
@@ -995,16 +1000,17 @@ def run_batched(args):
         "gpu_launches": int(lb), "gpu_launches_per_step": lb / args.steps,
         "query_kernel_groups": len([g for g in groups if not g.endswith(".coop")]),
         "phase_ms": {k: round(v, 4) for k, v in sorted(phase_ms.items())},
-        "autotune": autotune_summary(choices, defer),
+        "autotune": autotune_summary(choices, defer, getattr(args, "group_deferral", None)),
         "step_ms_median": float(np.median(b_ms)),
     }), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
-def autotune_summary(choices, defer):
-    """What the tuner chose: widths tried per problem and the threads-per-query
-    setting (deferral to the 256-thread cooperative kernel) per problem."""
+def autotune_summary(choices, defer, groups=None):
+    """What the tuner chose: widths tried per problem, the threads-per-query
+    setting (deferral to the 512-thread cooperative kernel) per problem, and
+    the batch-level choice per kernel group."""
     from paper_2004_02290_gb300 import autotune
 
     names = {(0, 0): "default deferral", (0, -1): "no deferral by candidates",
@@ -1018,6 +1024,8 @@ def autotune_summary(choices, defer):
            "deferral_choices": counts}
     if choices:
         out["widths_tried_per_problem_mean"] = float(np.mean([len(c.tried) for c in choices]))
+    if groups:
+        out["group_deferral"] = groups
     return out
 
 
@@ -1082,6 +1090,7 @@ def run_profile_case(args):
     if args.config == "batched" and args.batched_problem is None:
         ps = wl.gen_batched(args.batch_count, seed=3)
         widths, _, _, defer = batched_widths(ps, args, dev)
+        knn.knn_timing_enable(True)  # the tuner leaves it off
         pts = [torch.from_numpy(p_.points).to(dev) for p_ in ps]
         lab = [torch.from_numpy(p_.labels).to(dev) for p_ in ps]
         qs = [torch.from_numpy(p_.queries).to(dev) for p_ in ps]

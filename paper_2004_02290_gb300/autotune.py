@@ -9,10 +9,13 @@ settings by measurement on the GPU:
     query time scaled to all queries);
   - threads per query for heavy queries: at that width, it times the sample
     with the library's default deferral to the cooperative kernel (a block
-    of 256 threads for a query whose layers or row batches are large), with
+    of 512 threads for a query whose layers or row batches are large), with
     no deferral by candidate count, and with no deferral at all (every query
     on one warp of 32 threads), and keeps the fastest
-    (knn_index_set_deferral / knn_batch_set_deferral).
+    (knn_index_set_deferral / knn_batch_set_deferral).  In a batch the
+    problems of one kernel group share their launches, so the batch-level
+    pass (refine_batch_deferral) then times each group's deferral inside the
+    batched query itself.
 The warp kernel's own tile (32 rows a batch, 32 candidates a chunk, the
 resident blocks per SM) is fixed by the design and its occupancy sweep.
 
@@ -173,3 +176,67 @@ def tune_batch(problems, dev=None):
     t0 = time.perf_counter()
     choices = [tune_width(p.points, p.labels, p.queries, p.k, p.mode, dev=dev) for p in problems]
     return [c.width for c in choices], time.perf_counter() - t0, choices
+
+
+def refine_batch_deferral(problems, widths, defer, dev=None, reps: int = 3):
+    """Deferral settings per kernel group, measured in the batched query.
+
+    A group is the problems that share one launch (dimension, k up to 32 or
+    more, table kind).  For each group the batch is queried with the group's
+    problems on their own per-problem settings (`defer`), all on the
+    library's default and all on no deferral; the group's phase times (its
+    warp and cooperative launches, from the library's phase events) decide,
+    least of `reps` timings each.  Other groups keep their settings while one
+    is tried.  The library's phase timing is left off.  Returns (settings per
+    problem, seconds spent, {group phase: chosen option}).
+    """
+    import torch
+
+    t0 = time.perf_counter()
+    dev = dev or torch.device("cuda", torch.cuda.current_device())
+    pts = [torch.from_numpy(np.ascontiguousarray(p.points)).to(dev) for p in problems]
+    lab = [torch.from_numpy(np.ascontiguousarray(p.labels)).to(dev) for p in problems]
+    qs = [torch.from_numpy(np.ascontiguousarray(p.queries)).to(dev) for p in problems]
+    ks = [p.k for p in problems]
+    modes = [p.mode for p in problems]
+    b = knn.knn_batch_build(pts, lab, widths)
+    groups = {}
+    for i, p in enumerate(problems):
+        dense = b.info(i).table == knn.KNN_TABLE_DENSE
+        g = f"query.d{p.d}.{'k64' if p.k > 32 else 'k32'}.{'dense' if dense else 'hash'}"
+        groups.setdefault(g, []).append(i)
+    cur = [tuple(x) for x in defer]
+
+    def group_ms(g, settings):
+        for i in groups[g]:
+            b.set_deferral(i, *settings[i])
+        best = None
+        for _ in range(reps):
+            while knn.knn_timing_read():
+                pass
+            b.query(qs, ks, modes)
+            torch.cuda.synchronize(dev)
+            t = sum(ms for n, ms in knn.knn_timing_read() if n == g or n.startswith(g + "."))
+            best = t if best is None else min(best, t)
+        return best
+
+    knn.knn_timing_enable(True)
+    chosen = {}
+    try:
+        for g, members in groups.items():
+            options = {"per problem": list(cur)}
+            for name, x in (("default", (0, 0)), ("none", (-1, -1))):
+                opt = list(cur)
+                for i in members:
+                    opt[i] = x
+                options[name] = opt
+            times = {name: group_ms(g, opt) for name, opt in options.items()}
+            name = min(times, key=times.get)
+            cur = options[name]
+            for i in members:
+                b.set_deferral(i, *cur[i])
+            chosen[g] = name
+    finally:
+        knn.knn_timing_enable(False)
+        b.free()
+    return cur, time.perf_counter() - t0, chosen

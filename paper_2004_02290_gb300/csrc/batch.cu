@@ -485,6 +485,69 @@ struct Scratch {
     }
 };
 
+// Copies of pinned host inputs on the device's side stream, so that they
+// overlap work already queued on the caller's stream (the host link is the
+// bound of a host-buffer step).  begin() orders the side stream after
+// everything queued on the caller's stream so far (the staging buffer's
+// allocation, earlier copies); end() makes the caller's stream wait for the
+// copies.  The destructor ends them too, so that no exit path frees a
+// buffer that a copy still writes.
+struct SideCopies {
+    cudaStream_t s;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev = nullptr;
+    bool pending = false;
+    explicit SideCopies(cudaStream_t s_) : s(s_) {}
+    // false: no side stream (the caller copies on its own stream)
+    bool begin(int dev)
+    {
+        if (!open(dev)) return false;
+        pending = false;
+        if (cudaEventRecord(ev, s) != cudaSuccess || cudaStreamWaitEvent(side, ev, 0) != cudaSuccess) {
+            cudaGetLastError();
+            side = nullptr;
+            return false;
+        }
+        return true;
+    }
+    // The side stream without ordering it after the caller's: for copies
+    // into a buffer that is also allocated on the side stream.  The caller's
+    // stream waits for the side stream at end() even if nothing is copied.
+    bool open(int dev)
+    {
+        side = copy_stream(dev);
+        if (side && !ev && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            ev = nullptr;
+        }
+        if (!side || !ev) {
+            side = nullptr;
+            return false;
+        }
+        pending = true;
+        return true;
+    }
+    cudaError_t copy(void* dst, const void* src, size_t bytes)
+    {
+        pending = true;
+        return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, side);
+    }
+    cudaError_t end()
+    {
+        if (!pending) return cudaSuccess;
+        pending = false;
+        cudaError_t e = cudaEventRecord(ev, side);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev, 0);
+        if (e != cudaSuccess) cudaStreamSynchronize(side);
+        return e;
+    }
+    ~SideCopies()
+    {
+        end();
+        if (ev) cudaEventDestroy(ev);
+    }
+};
+
 knn_status fail(const char* msg, knn_status code)
 {
     set_error(msg);
@@ -534,7 +597,17 @@ knn_status batch_build_impl(int count, const float* const* points, const void* c
     phase_begin(s);
     {
         Scratch sc(s);
-        // ---- host inputs: copied into one device buffer (16-byte aligned slices) ----
+        SideCopies lab_copies(s);  // after sc: ends before sc frees the staging buffer
+        struct LateCopy {
+            void* dst;
+            const void* src;
+            size_t bytes;
+        };
+        std::vector<LateCopy> late_labels;
+        // ---- host inputs: copied into one device buffer (16-byte aligned slices);
+        // pinned host labels go over on the side stream once the boxes are
+        // read back, while the sort, cells and table kernels run (issued
+        // earlier, they held up the boxes' read-back on the copy engine) ----
         std::vector<const float*> pdev(points, points + count);
         std::vector<const void*> ldev(count, nullptr);
         if (labels) ldev.assign(labels, labels + count);
@@ -563,11 +636,15 @@ knn_status batch_build_impl(int count, const float* const* points, const void* c
                                             (size_t)n[i] * (size_t)d[i] * 4, cudaMemcpyHostToDevice, s);
                         pdev[i] = stage + p_at[i];
                     }
-                    if (l_at[i] != none && e == cudaSuccess) {
+                }
+                for (int i = 0; i < count && e == cudaSuccess; ++i) {
+                    if (l_at[i] == none) continue;
+                    if (pointer_kind(ldev[i], nullptr) == kMappedHost)
+                        late_labels.push_back(LateCopy{stage + l_at[i], ldev[i], (size_t)n[i] * 4});
+                    else
                         e = cudaMemcpyAsync(stage + l_at[i], ldev[i], (size_t)n[i] * 4,
                                             cudaMemcpyHostToDevice, s);
-                        ldev[i] = stage + l_at[i];
-                    }
+                    ldev[i] = stage + l_at[i];
                 }
                 if (e != cudaSuccess) return bail(cuda_error(e, "batch staged inputs"));
             }
@@ -637,6 +714,10 @@ knn_status batch_build_impl(int count, const float* const* points, const void* c
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return bail(cuda_error(e, "batch boxes"));
         phase_mark("box", s);
+        // the side stream may start the label copies from here on; they are
+        // issued once the sort is launched, so that the GPU has work while
+        // the host issues them
+        const bool lab_side = !late_labels.empty() && lab_copies.begin(dev);
 
         // ---- layouts ----
         int shift = 0;
@@ -756,10 +837,15 @@ knn_status batch_build_impl(int count, const float* const* points, const void* c
         count_launches(1);
         phase_mark("keys", s);
         e = radix_sort_pairs(ka, va, kb, vb, total, shift + ib, rtmp, &sk, &sv, s);
+        for (size_t c = 0; e == cudaSuccess && c < late_labels.size(); ++c) {
+            const LateCopy& lc = late_labels[c];
+            e = lab_side ? lab_copies.copy(lc.dst, lc.src, lc.bytes)
+                         : cudaMemcpyAsync(lc.dst, lc.src, lc.bytes, cudaMemcpyHostToDevice, s);
+        }
         phase_mark("sort", s);
         if (e == cudaSuccess)
             e = launch_cells(sk, total, stmp, cell_key, cell_start, b->gdev, s);
-        if (e != cudaSuccess) return bail(cuda_error(e, "batch sort"));
+        if (e != cudaSuccess) return bail(cuda_error(e, "batch sort and staged labels"));
         phase_mark("cells", s);
 
         // ---- tables ----
@@ -827,6 +913,8 @@ knn_status batch_build_impl(int count, const float* const* points, const void* c
                                                                b->rid);
         count_launches(1);
         if (any_labels) {
+            e = lab_copies.end();
+            if (e != cudaSuccess) return bail(cuda_error(e, "batch staged labels"));
             batch_labels_kernel<<<(unsigned)tiles.size(), 256, 0, s>>>(ddesc, dtiles, b->labels);
             count_launches(1);
         }
@@ -1112,6 +1200,7 @@ knn_status knn_batch_query(const ghn_batch* batch, const float* const* queries, 
     };
     std::vector<Copy> out_copies;
     void* stage = nullptr;
+    SideCopies q_copies(s);
     bool host_out = false;
     knn_status st = KNN_OK;
     {
@@ -1125,6 +1214,7 @@ knn_status knn_batch_query(const ghn_batch* batch, const float* const* queries, 
             words += count_words;
             return at;
         };
+        bool any_q = false, all_q_pinned = true;
         for (int i = 0; i < count && st == KNN_OK; ++i) {
             if (m[i] <= 0) continue;
             if (m[i] >= (1ll << 31) || k[i] < 1 || k[i] > kMaxK) break;  // plan_layout reports it
@@ -1135,6 +1225,8 @@ knn_status knn_batch_query(const ghn_batch* batch, const float* const* queries, 
             if (kind == kOtherGpu) st = fail("knn_batch_query: a buffer is device memory of another GPU", KNN_EINVAL);
             qd[i] = queries[i];
             if (kind == kHostMem || kind == kMappedHost) q_at[i] = take(mi * di);
+            any_q |= kind == kHostMem || kind == kMappedHost;
+            all_q_pinned &= kind != kHostMem;
             kind = pointer_kind(ids[i], &dp);
             if (kind == kOtherGpu) st = fail("knn_batch_query: a buffer is device memory of another GPU", KNN_EINVAL);
             idd[i] = kind == kMappedHost ? static_cast<int32_t*>(dp) : ids[i];
@@ -1155,7 +1247,14 @@ knn_status knn_batch_query(const ghn_batch* batch, const float* const* queries, 
                 host_out |= kind == kHostMem || kind == kMappedHost;
             }
         }
-        if (st == KNN_OK && words > 0) st = device_alloc(&stage, words * 4, s, "batch query staging");
+        // pinned host queries go over on the side stream, with the staging
+        // buffer allocated there, so that the copies overlap work still
+        // queued on the caller's stream (a build just launched); the kernels
+        // wait for them
+        const bool side = st == KNN_OK && words > 0 && any_q && all_q_pinned &&
+                          q_copies.open(batch->device);
+        if (st == KNN_OK && words > 0)
+            st = device_alloc(&stage, words * 4, side ? q_copies.side : s, "batch query staging");
         cudaError_t e = cudaSuccess;
         float* sw = static_cast<float*>(stage);
         for (int i = 0; st == KNN_OK && i < count; ++i) {
@@ -1164,7 +1263,9 @@ knn_status knn_batch_query(const ghn_batch* batch, const float* const* queries, 
             const size_t di = (size_t)batch->info[i].d;
             if (q_at[i] != none) {
                 if (e == cudaSuccess)
-                    e = cudaMemcpyAsync(sw + q_at[i], queries[i], mi * di * 4, cudaMemcpyHostToDevice, s);
+                    e = side ? q_copies.copy(sw + q_at[i], queries[i], mi * di * 4)
+                             : cudaMemcpyAsync(sw + q_at[i], queries[i], mi * di * 4,
+                                               cudaMemcpyHostToDevice, s);
                 qd[i] = sw + q_at[i];
             }
             if (i_at[i] != none) {
@@ -1180,6 +1281,8 @@ knn_status knn_batch_query(const ghn_batch* batch, const float* const* queries, 
                 out_copies.push_back(Copy{pred[i], pd[i], mi * 4});
             }
         }
+        const cudaError_t ee = q_copies.end();  // the kernels wait for the copies
+        if (e == cudaSuccess) e = ee;
         if (st == KNN_OK && e != cudaSuccess) st = cuda_error(e, "knn_batch_query: staging");
     }
     phase_mark("stage", s);

@@ -8,6 +8,10 @@
 
 namespace ghn {
 
+// A non-blocking stream per device for host-to-device copies that overlap
+// work on the caller's stream (created on first use; capi.cu), or null.
+cudaStream_t copy_stream(int dev);
+
 // Box of the points: per-block partials, then one block computes the extents.
 cudaError_t launch_box(const float* pts, long long n, int d, const Widths& w, float* partial,
                        int partial_blocks, BoxOut* out, cudaStream_t s);

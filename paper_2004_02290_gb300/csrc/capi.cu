@@ -974,6 +974,7 @@ void device_free(void* p, cudaStream_t s)
     if (p) cudaFreeAsync(p, s);
 }
 
+cudaStream_t copy_stream(int dev) { return side_stream(dev); }
 unsigned int heavy_rows_default(int d) { return heavy_rows_env(d); }
 unsigned int deferral_threshold(long long set, unsigned int dflt) { return deferral(set, dflt); }
 unsigned int heavy_cands_default() { return heavy_cands_env(); }

@@ -206,8 +206,8 @@ def test_full_size_batched_subset_matches_the_oracle():
 
 
 def test_batch_with_host_buffers_matches_device_buffers():
-    """knn_batch_build / knn_batch_query with host inputs, pinned and
-    pageable host outputs equal the all-device call."""
+    """knn_batch_build / knn_batch_query with host inputs and outputs
+    (pinned, pageable, mixed) equal the all-device call."""
     ps, _ = _problems()
     ps = ps[:8]
     ws = [p.w for p in ps]
@@ -217,15 +217,25 @@ def test_batch_with_host_buffers_matches_device_buffers():
     ref = b.query([_dev(p.queries) for p in ps], ks, modes, flags=knn.KNN_QUERY_CHECKED)
     torch.cuda.synchronize()
     b.free()
-    for pinned in (True, False):
-        def host(a):
+    # every buffer pinned, every buffer pageable, and a mix (pinned and
+    # pageable alternating over problems and arrays: copies on the side
+    # stream and on the caller's stream in one call)
+    # and pinned inputs with pageable outputs (the staging buffer, allocated
+    # on the side stream, then also holds outputs the kernels write)
+    for kind in ("pinned", "pageable", "mixed", "pinned inputs"):
+        turn = [0]
+
+        def host(a, output=False):
             t = torch.from_numpy(np.ascontiguousarray(a))
-            return t.pin_memory() if pinned else t
+            turn[0] += 1
+            pin = (kind == "pinned" or (kind == "mixed" and turn[0] % 3 != 0)
+                   or (kind == "pinned inputs" and not output))
+            return t.pin_memory() if pin else t
         b = knn.knn_batch_build([host(p.points) for p in ps], [host(p.labels) for p in ps], ws)
-        out = ([host(np.zeros((p.m, p.k), np.int32)) for p in ps],
-               [host(np.zeros((p.m, p.k), np.float32)) for p in ps],
+        out = ([host(np.zeros((p.m, p.k), np.int32), True) for p in ps],
+               [host(np.zeros((p.m, p.k), np.float32), True) for p in ps],
                [None if p.mode < 0 else host(np.zeros(p.m, np.int32 if p.mode == knn.KNN_VOTE
-                                                      else np.float32)) for p in ps])
+                                                      else np.float32), True) for p in ps])
         b.query([host(p.queries) for p in ps], ks, modes, flags=knn.KNN_QUERY_CHECKED, out=out)
         b.free()
         for j in range(len(ps)):
@@ -235,3 +245,35 @@ def test_batch_with_host_buffers_matches_device_buffers():
             if out[2][j] is not None:
                 assert np.array_equal(out[2][j].numpy().view(np.uint32),
                                       ref[2][j].cpu().numpy().view(np.uint32))
+
+
+def test_batch_deferral_refinement_chooses_per_group():
+    """The batch-level pass returns one of its options for every kernel group,
+    applied to all of the group's problems, and leaves phase timing off."""
+    from paper_2004_02290_gb300 import autotune
+
+    ps, _ = _problems()
+    ps = ps[:8]
+    start = [(0, -1)] * len(ps)
+    got, sec, groups = autotune.refine_batch_deferral(ps, [p.w for p in ps], start, reps=1)
+    assert sec > 0 and groups and len(got) == len(ps)
+    assert all(g.startswith("query.d") for g in groups)
+    options = {"per problem": (0, -1), "default": (0, 0), "none": (-1, -1)}
+    assert set(groups.values()) <= set(options)
+    for i, p in enumerate(ps):
+        assert tuple(got[i]) in options.values()
+    b = knn.knn_batch_build([_dev(p.points) for p in ps], [_dev(p.labels) for p in ps],
+                            [p.w for p in ps])
+    # every problem of a group got its group's option
+    members = {}
+    for i, p in enumerate(ps):
+        dense = b.info(i).table == knn.KNN_TABLE_DENSE
+        g = f"query.d{p.d}.{'k64' if p.k > 32 else 'k32'}.{'dense' if dense else 'hash'}"
+        members.setdefault(g, set()).add(tuple(got[i]))
+    assert set(members) == set(groups)
+    for g, opts in members.items():
+        assert opts == {options[groups[g]]}
+    b.query([_dev(p.queries) for p in ps], [p.k for p in ps], [p.mode for p in ps])
+    torch.cuda.synchronize()
+    b.free()
+    assert knn.knn_timing_read() == []
