@@ -277,3 +277,55 @@ def test_batch_deferral_refinement_chooses_per_group():
     torch.cuda.synchronize()
     b.free()
     assert knn.knn_timing_read() == []
+
+
+_ALLOC_FAIL = r"""
+import numpy as np, torch, sys
+sys.path.insert(0, %r)
+from paper_2004_02290_gb300 import knn, workloads as wl
+ps = wl.gen_batched(6, seed=5, n_lo=300, n_hi=5000, dims=(2, 3, 6), ks=(1, 5, 15))
+ws = [float(np.float32(0.08 * p.d / 3.0)) for p in ps]
+pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+def run():
+    b = knn.knn_batch_build([pin(p.points) for p in ps], [pin(p.labels) for p in ps], ws)
+    try:
+        out = ([pin(np.zeros((p.m, p.k), np.int32)) for p in ps],
+               [pin(np.zeros((p.m, p.k), np.float32)) for p in ps],
+               [pin(np.zeros(p.m, np.int32 if p.mode == knn.KNN_VOTE else np.float32))
+                for p in ps])
+        b.query([pin(p.queries) for p in ps], [p.k for p in ps], [p.mode for p in ps],
+                flags=knn.KNN_QUERY_CHECKED, out=out)
+        return out
+    finally:
+        b.free()
+try:
+    run()
+    print("NOFAIL")
+except knn.KnnError as e:
+    print("CODE", e.code)
+# the next build and query work and match the device-buffer path
+got = run()
+b = knn.knn_batch_build([torch.from_numpy(p.points).cuda() for p in ps],
+                        [torch.from_numpy(p.labels).cuda() for p in ps], ws)
+ref = b.query([torch.from_numpy(p.queries).cuda() for p in ps], [p.k for p in ps],
+              [p.mode for p in ps])
+torch.cuda.synchronize()
+b.free()
+ok = all(np.array_equal(got[0][i].numpy(), ref[0][i].cpu().numpy()) for i in range(len(ps)))
+print("AFTER", "same" if ok else "differ")
+"""
+
+
+def test_batch_host_buffers_survive_allocation_failure():
+    """An allocation that fails at a point of a batched build or query on
+    pinned host buffers (with copies on the side stream in flight) returns
+    KNN_ENOMEM, and the next call works and matches the device-buffer path."""
+    codes = []
+    for at in ("1", "3", "6", "10", "15", "20"):
+        env = dict(os.environ, GHN_FAIL_ALLOC_AT=at)
+        r = subprocess.run([sys.executable, "-c", _ALLOC_FAIL % ROOT], cwd=ROOT, env=env,
+                           capture_output=True, text=True, timeout=300)
+        assert r.returncode == 0, (at, r.stderr[-2000:])
+        assert "AFTER same" in r.stdout, (at, r.stdout)
+        codes.append(r.stdout.split()[1] if r.stdout.startswith("CODE") else "none")
+    assert codes.count("2") >= 4, codes  # KNN_ENOMEM at most of the points
