@@ -241,12 +241,11 @@ typedef struct ghn_plan ghn_plan;   /* a captured batch query (CUDA graph) */
  *   points[i]      host or device, n[i]*d[i] float32, row-major.
  *   labels         NULL, or an array whose entry i points to n[i] 32-bit
  *                  outputs (host or device), or is NULL for index i.
- *   Host inputs are copied into one device buffer (pinned host memory makes
- *   those copies asynchronous DMA transfers: pinned inputs must stay
- *   unchanged until `stream` has passed the build).  Points are copied on
+ *   Host inputs are copied into one device buffer.  Points are copied on
  *   `stream`; labels in pinned host memory on a library-owned side stream,
- *   once the boxes are read back, and `stream` waits for them before it
- *   reads them.
+ *   once the boxes are read back, while the build's kernels run (`stream`
+ *   waits for them before it reads them).  The call returns once every host
+ *   input has been read, so the caller may reuse those buffers then.
  *   n, d, cell_width, table   host arrays of count entries, as in knn_build
  *                  (table may be NULL: KNN_TABLE_AUTO for every index).
  * The total number of points must be below 2^31.  Errors as knn_build, and
@@ -266,11 +265,11 @@ knn_status knn_batch_info(const ghn_batch* batch, int32_t i, knn_index_info_t* i
  * Data pointers are host or device memory, as for knn_query: host queries
  * are copied into one device buffer (when every host query array is pinned,
  * on a library-owned side stream that starts at once, so that the copies
- * overlap work already queued on `stream`, which waits for them; pinned
- * inputs must stay unchanged until `stream` has passed the call); outputs
- * in pinned host memory are written by the kernels directly, other host
- * outputs are staged on the device and copied out; host outputs are
- * complete when the call returns.
+ * overlap work already queued on `stream`, which waits for them; the call
+ * returns once every host query has been read, so the caller may reuse
+ * those buffers then); outputs in pinned host memory are written by the
+ * kernels directly, other host outputs are staged on the device and copied
+ * out; host outputs are complete when the call returns.
  * With knn_timing_enable on, the call records its phases (stage, one per
  * kernel group "query.d<d>.<k32|k64>.<dense|hash>", copy); knn_batch_build
  * records stage, box, keys, sort, cells, table, gather.

@@ -497,6 +497,7 @@ struct SideCopies {
     cudaStream_t side = nullptr;
     cudaEvent_t ev = nullptr;
     bool pending = false;
+    bool recorded = false;  // end() recorded the copies' event
     explicit SideCopies(cudaStream_t s_) : s(s_) {}
     // false: no side stream (the caller copies on its own stream)
     bool begin(int dev)
@@ -539,7 +540,17 @@ struct SideCopies {
         cudaError_t e = cudaEventRecord(ev, side);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev, 0);
         if (e != cudaSuccess) cudaStreamSynchronize(side);
+        recorded = e == cudaSuccess;
         return e;
+    }
+    // The host waits until the copies have read their sources, so that the
+    // caller may reuse its pinned buffers once the call returns (the GPU
+    // keeps the work queued on the caller's stream meanwhile).
+    cudaError_t wait_host()
+    {
+        if (!recorded) return cudaSuccess;
+        recorded = false;
+        return cudaEventSynchronize(ev);
     }
     ~SideCopies()
     {
@@ -917,6 +928,8 @@ knn_status batch_build_impl(int count, const float* const* points, const void* c
             if (e != cudaSuccess) return bail(cuda_error(e, "batch staged labels"));
             batch_labels_kernel<<<(unsigned)tiles.size(), 256, 0, s>>>(ddesc, dtiles, b->labels);
             count_launches(1);
+            e = lab_copies.wait_host();  // pinned labels may be reused after the call
+            if (e != cudaSuccess) return bail(cuda_error(e, "batch staged labels"));
         }
         e = cudaGetLastError();
         phase_mark("gather", s);
@@ -1201,6 +1214,7 @@ knn_status knn_batch_query(const ghn_batch* batch, const float* const* queries, 
     std::vector<Copy> out_copies;
     void* stage = nullptr;
     SideCopies q_copies(s);
+    cudaEvent_t q_read = nullptr;  // pinned queries copied on `s` have been read
     bool host_out = false;
     knn_status st = KNN_OK;
     {
@@ -1214,7 +1228,7 @@ knn_status knn_batch_query(const ghn_batch* batch, const float* const* queries, 
             words += count_words;
             return at;
         };
-        bool any_q = false, all_q_pinned = true;
+        bool any_q = false, all_q_pinned = true, any_q_pinned = false;
         for (int i = 0; i < count && st == KNN_OK; ++i) {
             if (m[i] <= 0) continue;
             if (m[i] >= (1ll << 31) || k[i] < 1 || k[i] > kMaxK) break;  // plan_layout reports it
@@ -1227,6 +1241,7 @@ knn_status knn_batch_query(const ghn_batch* batch, const float* const* queries, 
             if (kind == kHostMem || kind == kMappedHost) q_at[i] = take(mi * di);
             any_q |= kind == kHostMem || kind == kMappedHost;
             all_q_pinned &= kind != kHostMem;
+            any_q_pinned |= kind == kMappedHost;
             kind = pointer_kind(ids[i], &dp);
             if (kind == kOtherGpu) st = fail("knn_batch_query: a buffer is device memory of another GPU", KNN_EINVAL);
             idd[i] = kind == kMappedHost ? static_cast<int32_t*>(dp) : ids[i];
@@ -1283,6 +1298,11 @@ knn_status knn_batch_query(const ghn_batch* batch, const float* const* queries, 
         }
         const cudaError_t ee = q_copies.end();  // the kernels wait for the copies
         if (e == cudaSuccess) e = ee;
+        // pinned queries copied on the caller's stream: an event, so that the
+        // call can return once they have been read
+        if (st == KNN_OK && e == cudaSuccess && !side && any_q_pinned &&
+            cudaEventCreateWithFlags(&q_read, cudaEventDisableTiming) == cudaSuccess)
+            e = cudaEventRecord(q_read, s);
         if (st == KNN_OK && e != cudaSuccess) st = cuda_error(e, "knn_batch_query: staging");
     }
     phase_mark("stage", s);
@@ -1307,6 +1327,16 @@ knn_status knn_batch_query(const ghn_batch* batch, const float* const* queries, 
         }
         if (p.dev_buf) device_free(p.dev_buf, s);
         p.dev_buf = nullptr;
+    }
+    {
+        // pinned queries may be reused after the call
+        cudaError_t e = q_copies.wait_host();
+        if (q_read) {
+            const cudaError_t e2 = cudaEventSynchronize(q_read);
+            if (e == cudaSuccess) e = e2;
+            cudaEventDestroy(q_read);
+        }
+        if (st == KNN_OK && e != cudaSuccess) st = cuda_error(e, "knn_batch_query: staging");
     }
     if (stage) device_free(stage, s);
     if (host_out) {

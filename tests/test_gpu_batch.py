@@ -329,3 +329,47 @@ def test_batch_host_buffers_survive_allocation_failure():
         assert "AFTER same" in r.stdout, (at, r.stdout)
         codes.append(r.stdout.split()[1] if r.stdout.startswith("CODE") else "none")
     assert codes.count("2") >= 4, codes  # KNN_ENOMEM at most of the points
+
+
+def test_batch_pinned_inputs_on_a_user_stream():
+    """Pinned host inputs on a non-default stream: the build is still running
+    on that stream when the query's staging copies start on the library's
+    side stream.  Each call returns only once its host inputs have been read,
+    so overwriting them right after the call changes nothing; the results
+    equal the device-buffer call's."""
+    ps, _ = _problems()
+    ps = ps[:8]
+    ws = [p.w for p in ps]
+    ks = [p.k for p in ps]
+    modes = [p.mode for p in ps]
+    b = knn.knn_batch_build([_dev(p.points) for p in ps], [_dev(p.labels) for p in ps], ws)
+    ref = b.query([_dev(p.queries) for p in ps], ks, modes, flags=knn.KNN_QUERY_CHECKED)
+    torch.cuda.synchronize()
+    b.free()
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    s = torch.cuda.Stream()
+    for rep in range(2):
+        pts = [pin(p.points) for p in ps]
+        lab = [pin(p.labels) for p in ps]
+        b = knn.knn_batch_build(pts, lab, ws, stream=s)
+        for t in pts + lab:
+            t.view(torch.int32).fill_(-7)  # the build has read them
+        qs = [pin(p.queries) for p in ps]
+        got = ([torch.empty((p.m, p.k), dtype=torch.int32, device="cuda") for p in ps],
+               [torch.empty((p.m, p.k), dtype=torch.float32, device="cuda") for p in ps],
+               [None if p.mode < 0 else
+                torch.empty(p.m, dtype=torch.int32 if p.mode == knn.KNN_VOTE else torch.float32,
+                            device="cuda") for p in ps])
+        # device outputs: nothing in the call waits for the kernels
+        b.query(qs, ks, modes, stream=s, out=got)
+        for t in qs:
+            t.fill_(float("nan"))  # the query has read them
+        s.synchronize()
+        b.free()
+        for j in range(len(ps)):
+            assert np.array_equal(got[0][j].cpu().numpy(), ref[0][j].cpu().numpy()), (rep, j)
+            assert np.array_equal(got[1][j].cpu().numpy().view(np.uint32),
+                                  ref[1][j].cpu().numpy().view(np.uint32)), (rep, j)
+            if got[2][j] is not None:
+                assert np.array_equal(got[2][j].cpu().numpy().view(np.uint32),
+                                      ref[2][j].cpu().numpy().view(np.uint32)), (rep, j)
