@@ -894,49 +894,44 @@ __device__ __forceinline__ bool walk_query(const QueryArgs& a, long long qid, Wa
                 sm.ao[lane] = sa - (incl - tot);
                 sm.bo[lane] = sb - (incl - lb);
                 __syncwarp();
-                // chunks of 32 candidates; the next chunk's rows are loaded
-                // while the current one is offered to the buffer
+                // chunks of 32 candidates, one per lane.  Each chunk loads its
+                // own rows: with 6 to 8 resident blocks an SM, other warps
+                // cover the load, and a row prefetched a chunk ahead cost a
+                // copy per chunk and more spilled registers (measured 3%
+                // slower on the d=6 batched group and on large_cls)
                 constexpr int P = row_floats(D);
                 // each lane's cursor: the lane `own` whose ranges hold its
                 // next candidate (a binary search for the first chunk, then
                 // forward moves only when a chunk step leaves own's ranges)
                 // and a copy of own's range offsets
                 unsigned int own = 0u, o_end = 0u, o_mid = 0u, o_ao = 0u, o_bo = 0u;
-                Row<P> nrow;
-                unsigned int npos = 0u;
                 if (lane < total) {
                     own = owner_of(sm.end, lane);
                     o_end = sm.end[own];
                     o_mid = sm.mid[own];
                     o_ao = sm.ao[own];
                     o_bo = sm.bo[own];
-                    const unsigned int t0 = (unsigned int)lane;
-                    npos = (t0 < o_mid ? o_ao : o_bo) + t0;
-                    nrow.load(a.rows, npos);
                 }
                 // the k-th squared distance (+inf while the buffer is short)
                 float kf = tk.count == tk.k ? __uint_as_float((unsigned)(tk.kth >> 32)) : INFINITY;
                 for (unsigned int cb = 0; cb < total; cb += 32u) {
                     const unsigned int t = cb + lane;
-                    const Row<P> row = nrow;
-                    const unsigned int pos = npos;
-                    const unsigned int tn = t + 32u;
-                    if (tn < total) {
-                        if (tn >= o_end) {
+                    bool pass = false;
+                    float acc = 0.0f;
+                    unsigned int pos = 0u;
+                    if (t < total) {
+                        if (t >= o_end) {
                             do {
                                 ++own;
-                            } while (sm.end[own] <= tn);  // ends at 31 at the latest
+                            } while (sm.end[own] <= t);  // ends at 31 at the latest
                             o_end = sm.end[own];
                             o_mid = sm.mid[own];
                             o_ao = sm.ao[own];
                             o_bo = sm.bo[own];
                         }
-                        npos = (tn < o_mid ? o_ao : o_bo) + tn;
-                        nrow.load(a.rows, npos);
-                    }
-                    bool pass = false;
-                    float acc = 0.0f;
-                    if (t < total) {
+                        pos = (t < o_mid ? o_ao : o_bo) + t;
+                        Row<P> row;
+                        row.load(a.rows, pos);
                         acc = sq_dist<D, P>(s.q, row);
                         pass = acc <= kf;
                     }
